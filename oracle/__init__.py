@@ -1,0 +1,217 @@
+"""Oracle for the block-oriented one-sided Jacobi (H)SVD -- TEST INFRASTRUCTURE.
+
+A plain, slow, obviously correct CPU implementation of what the CUDA path
+computes, written from the paper (Novakovic, "A hierarchically blocked Jacobi
+SVD algorithm for single and multiple graphics processing units") and
+independent of the CUDA path: the two share no code, header, table or
+generator.  Only tests/, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline / reference legs may import this package.  The product path
+never does.
+
+Numerics are FP64 in plain C (``jacobi_oracle.c``, compiled with
+``-ffp-contract=off``); pivot strategies are plain Python (``pivots.py``).
+
+Pins (tests/test_oracle_*.py): closed-form 2x2 rotations, Table B.1 of the
+paper (statistical, exact rational arithmetic), Lemma 3.2 and the n = 4
+tables, Alg. 3.1 == Alg. 3.2 for small orders, the 1-factorisation
+invariant, planted singular values, LAPACK (numpy) and mpmath SVDs, the
+reconstruction / orthogonality invariants, eigenvalues of G J G^T for the
+HSVD, and central finite differences for the adjoint.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from . import pivots
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jacobi_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libjacobi_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EPS = 2.0 ** -53
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C file with gcc (plain C, no fused multiply-add
+    contraction) into oracle/_build/."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            lib.jo_rot.argtypes = [D, D, D, I, I, P, P]
+            lib.jo_rot.restype = I
+            lib.jo_rot_batch.argtypes = [I, P, P, P, P, I, P, P, P]
+            lib.jo_hestenes.argtypes = [I, I, I, P, I, P, I, P, I, I, I, D, P, P]
+            lib.jo_block_pstep.argtypes = [I, I, I, I, P, I, P, I, P, I, P, I, P]
+            lib.jo_block_svd.argtypes = [I, I, I, I, P, I, P, I, P, I, I, P, I, I, P, P]
+            lib.jo_colnorms.argtypes = [I, I, P, I, P]
+            lib.jo_svd_adjoint.argtypes = [I, I, P, P, P, P, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _fortran(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+# ---------------------------------------------------------------------------
+def rotation(hpp, hqq, hpq, hyperbolic=False, cs_form=2):
+    """Eqs. (4.3)-(4.6): (cs, tn, proper) for arrays of 2x2 pivot data."""
+    hpp = np.ascontiguousarray(np.atleast_1d(hpp), dtype=np.float64)
+    hqq = np.ascontiguousarray(np.broadcast_to(hqq, hpp.shape), dtype=np.float64)
+    hpq = np.ascontiguousarray(np.broadcast_to(hpq, hpp.shape), dtype=np.float64)
+    t = np.ascontiguousarray(np.broadcast_to(np.where(hyperbolic, -1, 1), hpp.shape), dtype=np.int32)
+    n = hpp.size
+    cs = np.empty(n)
+    tn = np.empty(n)
+    pr = np.empty(n, dtype=np.int32)
+    _load().jo_rot_batch(n, _ptr(hpp), _ptr(hqq), _ptr(hpq), _ptr(t), cs_form, _ptr(cs), _ptr(tn), _ptr(pr))
+    return cs, tn, pr.astype(bool)
+
+
+def strategy_array(name: str, n: int) -> np.ndarray:
+    return pivots.to_array(pivots.strategy(name, n))
+
+
+def hestenes(A, strategy: str = "rR", nplus: int | None = None, max_sweeps: int = 100,
+             with_v: bool = True, nhat: float | None = None):
+    """Pointwise one-sided Jacobi on A (m x n, m >= n, n even); returns the raw
+    results: G = A V (unsorted), V (or W = V^{-T} for the HSVD), statistics."""
+    G = _fortran(A).copy(order="F")
+    m, n = G.shape
+    nplus = n if nplus is None else nplus
+    V = np.asfortranarray(np.eye(n)) if with_v else None
+    if n % 2:
+        # odd n (Eq. (3.1): n p-steps of (n-1)/2 pairs): the strategy of order
+        # n+1 with every pair that holds the phantom index n left out
+        full = pivots.strategy(strategy, n + 1)
+        tab = np.ascontiguousarray(pivots.to_array([[p for p in st if p[1] < n] for st in full]))
+    else:
+        tab = np.ascontiguousarray(strategy_array(strategy, n))
+    stats = np.zeros(5, dtype=np.int64)
+    per = np.zeros(max_sweeps, dtype=np.int64)
+    _load().jo_hestenes(m, n, nplus, _ptr(G), m, _ptr(V) if V is not None else None, n,
+                        _ptr(tab), tab.shape[0], tab.shape[1], max_sweeps,
+                        float(m if nhat is None else nhat), _ptr(stats), _ptr(per))
+    return dict(G=G, V=V, sweeps=int(stats[0]), converged=bool(stats[1]),
+                rotations=int(stats[2]), proper=int(stats[3]), swaps=int(stats[4]),
+                rotations_per_sweep=per[: stats[0]].copy())
+
+
+def colnorms(G) -> np.ndarray:
+    G = _fortran(G)
+    m, n = G.shape
+    s = np.empty(n)
+    _load().jo_colnorms(m, n, _ptr(G), m, _ptr(s))
+    return s
+
+
+def finish(G, V, nplus: int | None = None, hyperbolic_w: bool = False):
+    """Sigma extraction and the final order: sigma_i = ||g_i||, u_i = g_i/sigma_i,
+    stable sort descending (within the J+ and J- blocks for the HSVD);
+    for the HSVD the accumulated W is turned into V = J W J."""
+    G = _fortran(G)
+    m, n = G.shape
+    nplus = n if nplus is None else nplus
+    s = colnorms(G)
+    if nplus == n:
+        order = np.argsort(-s, kind="stable")
+    else:
+        order = np.concatenate([np.argsort(-s[:nplus], kind="stable"),
+                                nplus + np.argsort(-s[nplus:], kind="stable")])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        U = np.where(s[order] > 0, G[:, order] / s[order], 0.0)
+    Vout = None
+    if V is not None:
+        W = np.asarray(V)
+        if hyperbolic_w:
+            j = np.where(np.arange(n) < nplus, 1.0, -1.0)
+            W = j[:, None] * W * j[None, :]
+        Vout = W[:, order]
+    return U, s[order], Vout
+
+
+def svd(A, strategy: str = "rR", max_sweeps: int = 100):
+    """Full oracle SVD A = U diag(S) V^T (pointwise Hestenes + finish)."""
+    r = hestenes(A, strategy=strategy, max_sweeps=max_sweeps)
+    U, S, V = finish(r["G"], r["V"])
+    return U, S, V, r
+
+
+def hsvd(G, nplus: int, strategy: str = "rR", max_sweeps: int = 100):
+    """Oracle HSVD G = U diag(S) V^T with V^T J V = J, J = diag(I_nplus, -I)."""
+    r = hestenes(G, strategy=strategy, nplus=nplus, max_sweeps=max_sweeps)
+    U, S, V = finish(r["G"], r["V"], nplus=nplus, hyperbolic_w=True)
+    return U, S, V, r
+
+
+def block_pstep(G, V, b: int, step_pairs, inner_table, nplus: int | None = None,
+                inner_sweeps: int = 1):
+    """One p-step of the block-oriented method on copies of G and V."""
+    G = _fortran(G).copy(order="F")
+    V = _fortran(V).copy(order="F")
+    m, n = G.shape
+    nplus = n if nplus is None else nplus
+    sp = np.ascontiguousarray(np.asarray(step_pairs, dtype=np.int32).reshape(-1, 2))
+    it = np.ascontiguousarray(np.asarray(inner_table, dtype=np.int32))
+    stats = np.zeros(4, dtype=np.int64)
+    _load().jo_block_pstep(m, n, nplus, b, _ptr(G), m, _ptr(V), n, _ptr(sp), sp.shape[0],
+                           _ptr(it), inner_sweeps, _ptr(stats))
+    return G, V, dict(rotations=int(stats[0]), proper=int(stats[1]),
+                      updated=int(stats[2]), breakdowns=int(stats[3]))
+
+
+def block_svd(A, b: int, strategy: str = "rR", inner_strategy: str | None = None,
+              nplus: int | None = None, inner_sweeps: int = 1, max_sweeps: int = 30):
+    """The block-oriented method (Sec. 2, 4) on CPU: raw G, V and statistics."""
+    G = _fortran(A).copy(order="F")
+    m, n = G.shape
+    if n % (2 * b):
+        raise ValueError("n must be a multiple of 2b")
+    nb = n // b
+    nplus = n if nplus is None else nplus
+    V = np.asfortranarray(np.eye(n))
+    tab = np.ascontiguousarray(strategy_array(strategy, nb))
+    it = np.ascontiguousarray(strategy_array(inner_strategy or strategy, 2 * b))
+    stats = np.zeros(6, dtype=np.int64)
+    per = np.zeros(max_sweeps, dtype=np.int64)
+    _load().jo_block_svd(m, n, nplus, b, _ptr(G), m, _ptr(V), n, _ptr(tab), tab.shape[0],
+                         tab.shape[1], _ptr(it), inner_sweeps, max_sweeps, _ptr(stats), _ptr(per))
+    return dict(G=G, V=V, sweeps=int(stats[0]), converged=bool(stats[1]), rotations=int(stats[2]),
+                proper=int(stats[3]), updated=int(stats[4]), breakdowns=int(stats[5]),
+                proper_per_sweep=per[: stats[0]].copy())
+
+
+def svd_adjoint(U, S, V, dU, dS, dV) -> np.ndarray:
+    """Reverse-mode derivative dA of A = U diag(S) V^T (published formula)."""
+    U, V, dU, dV = (_fortran(x) for x in (U, V, dU, dV))
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    dS = np.ascontiguousarray(dS, dtype=np.float64)
+    m, n = U.shape
+    dA = np.asfortranarray(np.empty((m, n)))
+    _load().jo_svd_adjoint(m, n, _ptr(U), _ptr(S), _ptr(V), _ptr(dU), _ptr(dS), _ptr(dV), _ptr(dA))
+    return dA

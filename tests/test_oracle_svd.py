@@ -1,0 +1,138 @@
+"""Pins of the oracle's SVD / HSVD against what mathematics and the paper fix:
+planted singular values, LAPACK (numpy) and mpmath SVDs, the invariants
+||A - U S V^T||, ||U^T U - I||, ||V^T V - I||, the eigenvalues of G J G^T for
+the HSVD (Eq. (2.10), the error metric (6.1)), V^T J V = J, determinism."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1401_2720_gb300 import inputs as I
+
+EPS = 2.0 ** -53
+
+
+def _orth(X):
+    return np.abs(X.T @ X - np.eye(X.shape[1])).max()
+
+
+@pytest.mark.parametrize("strategy", ["modulus", "rR", "R", "C", "rC"])
+def test_planted_sigma(strategy):
+    m, n = 96, 48
+    s_true = I.geometric(n, 1.0, 1e-6)
+    A = I.planted(m, n, s_true, seed=3)
+    U, S, V, r = O.svd(A, strategy=strategy)
+    assert r["converged"]
+    assert np.max(np.abs(S - s_true)) <= 50 * np.sqrt(n) * EPS * s_true[0]
+    assert _orth(U) <= 50 * n * EPS and _orth(V) <= 50 * n * EPS
+    assert np.linalg.norm(A - (U * S) @ V.T) <= 50 * n * EPS * np.linalg.norm(A)
+
+
+def test_matches_lapack_and_vectors():
+    rng = np.random.default_rng(4)
+    A = np.asfortranarray(rng.standard_normal((80, 64)))
+    U, S, V, _ = O.svd(A)
+    Ul, Sl, Vlt = np.linalg.svd(A, full_matrices=False)
+    assert np.max(np.abs(S - Sl)) <= 100 * EPS * Sl[0]
+    # singular vectors agree up to sign (well separated spectrum)
+    sgn = np.sign(np.sum(U * Ul, axis=0))
+    assert np.max(np.abs(U * sgn - Ul)) < 1e-9
+    assert np.max(np.abs(V * sgn - Vlt.T)) < 1e-9
+
+
+def test_matches_mpmath_high_precision():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(5)
+    A = np.asfortranarray(rng.standard_normal((7, 4)) * np.array([1.0, 1e-3, 10.0, 1e-5]))
+    U, S, V, _ = O.svd(A)
+    s_mp = mpmath.svd_r(mpmath.matrix(A.tolist()), compute_uv=False)
+    s_ref = np.sort(np.array([float(x) for x in s_mp]))[::-1]
+    # one-sided Jacobi is relatively accurate for column-scaled inputs
+    assert np.max(np.abs(S - s_ref) / s_ref) <= 1e-13
+
+
+def test_tiny_bruteforce_2x2():
+    A = np.asfortranarray(np.array([[3.0, 1.0], [1.0, 2.0]]))
+    U, S, V, _ = O.svd(A)
+    ev = np.linalg.eigvalsh(A.T @ A)
+    assert np.allclose(np.sort(S ** 2), np.sort(ev), rtol=1e-15, atol=0)
+
+
+def test_hsvd_eigenvalues_and_j_orthogonality():
+    rng = np.random.default_rng(6)
+    m, n, npl = 40, 24, 10
+    G = np.asfortranarray(rng.standard_normal((m, n)))
+    U, S, V, r = O.hsvd(G, npl)
+    assert r["converged"]
+    j = np.where(np.arange(n) < npl, 1.0, -1.0)
+    J = np.diag(j)
+    # Eq. (2.10): G = U S V^T with V^T J V = J
+    assert np.linalg.norm(G - (U * S) @ V.T) <= 1e3 * EPS * np.linalg.norm(G) * np.linalg.norm(V) ** 2
+    assert np.abs(V.T @ J @ V - J).max() <= 1e3 * n * EPS * np.linalg.norm(V, 2) ** 2
+    assert _orth(U) <= 50 * n * EPS
+    # sigma_i^2 j_i are the non-zero eigenvalues of G J G^T
+    lam = np.linalg.eigvalsh(G @ J @ G.T)
+    lam = lam[np.argsort(-np.abs(lam))][:n]
+    mine = S ** 2 * j
+    assert np.allclose(np.sort(mine), np.sort(lam), rtol=0, atol=1e-12 * np.abs(lam).max())
+    # sign blocks sorted non-increasingly
+    assert np.all(np.diff(S[:npl]) <= 0) and np.all(np.diff(S[npl:]) <= 0)
+
+
+def test_hsvd_with_identity_j_is_svd():
+    rng = np.random.default_rng(7)
+    G = np.asfortranarray(rng.standard_normal((30, 20)))
+    a = O.svd(G)
+    b = O.hsvd(G, 20)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+
+
+def test_deterministic():
+    A = I.planted(64, 32, I.geometric(32, 1, 1e-4), seed=8)
+    a = O.svd(A)
+    b = O.svd(A)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("b", [2, 4, 8])
+def test_block_method_agrees_with_pointwise(b):
+    m, n = 72, 48
+    s_true = I.geometric(n, 1.0, 1e-5)
+    A = I.planted(m, n, s_true, seed=9)
+    r = O.block_svd(A, b, strategy="rR")
+    assert r["converged"] and r["breakdowns"] == 0
+    U, S, V = O.finish(r["G"], r["V"])
+    U2, S2, V2, _ = O.svd(A)
+    assert np.max(np.abs(S - s_true)) <= 50 * np.sqrt(n) * EPS * s_true[0]
+    assert np.max(np.abs(S - S2)) <= 50 * np.sqrt(n) * EPS * s_true[0]
+    assert _orth(U) <= 50 * n * EPS and _orth(V) <= 50 * n * EPS
+    # G = A V holds throughout (Eq. (2.5))
+    assert np.linalg.norm(r["G"] - A @ r["V"]) <= 50 * n * EPS * np.linalg.norm(A)
+
+
+def test_block_pstep_invariants():
+    """One p-step: G' = A V', V' orthogonal, and the pair of block-columns it
+    touched became (relatively) closer to orthogonal."""
+    from oracle import pivots as P
+
+    m, n, b = 64, 32, 4
+    A = I.planted(m, n, I.geometric(n, 1, 1e-3), seed=10)
+    tab = P.strategy("rR", n // b)
+    inner = P.to_array(P.strategy("rR", 2 * b))
+    G, V, st = O.block_pstep(A, np.eye(n), b, tab[0], inner)
+    assert st["updated"] == len(tab[0]) and st["breakdowns"] == 0
+    assert _orth(V) <= 50 * n * EPS
+    assert np.linalg.norm(G - A @ V) <= 50 * n * EPS * np.linalg.norm(A)
+
+    def off(X, P_, Q_):
+        cols = list(range(P_ * b, P_ * b + b)) + list(range(Q_ * b, Q_ * b + b))
+        Y = X[:, cols]
+        H = Y.T @ Y
+        d = np.sqrt(np.diag(H))
+        Hn = H / np.outer(d, d)
+        return np.linalg.norm(Hn - np.eye(2 * b))
+
+    for P_, Q_ in tab[0]:
+        assert off(G, P_, Q_) < off(A, P_, Q_)
