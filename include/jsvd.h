@@ -1,0 +1,159 @@
+/*
+ * jsvd.h -- C ABI of the GB300-native block-oriented one-sided Jacobi (H)SVD.
+ *
+ * Method: V. Novakovic, "A hierarchically blocked Jacobi SVD algorithm for
+ * single and multiple graphics processing units" (SIAM J. Sci. Comput.).
+ * One block p-step (Sec. 2, Sec. 4) processes every pivot block-pair (G_p, G_q)
+ * of a parallel p-strategy (Sec. 3) independently:
+ *   H_pq = [G_p G_q]^T [G_p G_q],  H_pq = R^T R (Cholesky, Eq. (2.7), Sec. 4.1)
+ *   one inner sweep of the pointwise one-sided Jacobi method on R with the
+ *   rotations of Eqs. (4.3)-(4.6), accumulated into V'           (Sec. 4.3)
+ *   [G_p G_q] := [G_p G_q] V',  [V_p V_q] := [V_p V_q] V'          (Eq. (2.9))
+ * Block sweeps repeat until a sweep performs no proper rotation (Sec. 4.5).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are FP64, column-major: element (i,j) of X with leading
+ *    dimension ldx is X[i + j*ldx].
+ *  - Pointers named "device" must be CUDA device (or managed) memory on the
+ *    context's device; the caller owns them.  The library owns its workspace.
+ *  - All GPU work is ordered on the stream given to jsvd_create /
+ *    jsvd_set_stream (NULL = the legacy default stream).  Calls that report
+ *    statistics (info) synchronise that stream before returning.
+ *  - Return value: 0 on success; -i if argument i (1-based) is invalid;
+ *    a positive JSVD_* status otherwise.  jsvd_status_string() describes it,
+ *    jsvd_last_error() gives the context's last detailed message.
+ *  - Nothing here is thread-safe on one context; use one context per thread.
+ */
+#ifndef JSVD_H
+#define JSVD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define JSVD_SUCCESS          0
+#define JSVD_NOT_CONVERGED    1  /* sweep limit reached; results are the last iterate */
+#define JSVD_ERR_NONFINITE    2  /* input holds Inf or NaN; outputs untouched */
+#define JSVD_ERR_CUDA         3  /* a CUDA call failed; see jsvd_last_error() */
+#define JSVD_ERR_ALLOC        4  /* workspace allocation failed */
+#define JSVD_ERR_UNSUPPORTED  5  /* option combination not supported */
+#define JSVD_ERR_TIMEOUT      6  /* a bounded device-side wait gave up */
+
+/* ---- pivot strategies (Sec. 3) ---------------------------------------- */
+#define JSVD_STRAT_MODULUS   0  /* modulus ordering: odd-order modulus completed to even order */
+#define JSVD_STRAT_ROW       1  /* R||: p-strategy closest to row-cyclic (Def. 3.1, Alg. 3.1/3.2) */
+#define JSVD_STRAT_COL       2  /* C||: p-strategy closest to column-cyclic */
+#define JSVD_STRAT_ROW_REV   3  /* reverse of R|| (the paper's default) */
+#define JSVD_STRAT_COL_REV   4  /* reverse of C|| */
+
+/* ---- precision modes -------------------------------------------------- */
+#define JSVD_PREC_FP64       0  /* all sweeps in FP64 */
+#define JSVD_PREC_MIXED      1  /* FP32 block sweeps, then FP64 sweeps to convergence */
+
+typedef struct jsvd_ctx *jsvd_ctx_t;
+
+typedef struct {
+    int b;               /* block-column width: 8, 16 or 32 (0: chosen by size) */
+    int strategy;        /* outer p-strategy, JSVD_STRAT_* (Sec. 3) */
+    int inner_strategy;  /* inner p-strategy; -1: same as strategy (Sec. 4.3) */
+    int inner_sweeps;    /* M_s: 1 = block-oriented variant, >1 = up to that many
+                            inner sweeps (full block variant), Sec. 4.3 */
+    int max_sweeps;      /* limit on block sweeps (0: 30) */
+    int precision;       /* JSVD_PREC_* */
+    int sort;            /* 1: sigma non-increasing (per sign block for the HSVD) */
+} jsvd_opts;
+
+typedef struct {
+    int sweeps;                 /* FP64 block sweeps performed */
+    int sweeps_low;             /* FP32 block sweeps (mixed precision), else 0 */
+    int converged;              /* 1 if the last sweep had no proper rotation */
+    int b;                      /* block width used */
+    long long rotations;        /* rotations applied (all inner pairs with rho = 1) */
+    long long proper_rotations; /* rotations with cos != 1 (Sec. 4.3 subphase 4) */
+    long long pairs_updated;    /* block pairs whose V' != I (Eq. (2.9) applied) */
+    long long breakdowns;       /* non-positive Cholesky pivots met (column zeroed) */
+    double off_norm;            /* max |h_ij|/sqrt(h_ii h_jj) over the pivot Grams of
+                                   the last sweep */
+} jsvd_info;
+
+/* Fill *opts with the defaults: b = 0, strategy = JSVD_STRAT_ROW_REV,
+ * inner_strategy = -1, inner_sweeps = 1, max_sweeps = 30, FP64, sort = 1. */
+void jsvd_default_opts(jsvd_opts *opts);
+
+/* Create a context on CUDA device `device`, issuing work on `stream`
+ * (a cudaStream_t, may be NULL).  The context owns a growable workspace. */
+int jsvd_create(jsvd_ctx_t *ctx, int device, void *stream);
+int jsvd_destroy(jsvd_ctx_t ctx);
+int jsvd_set_stream(jsvd_ctx_t ctx, void *stream);
+const char *jsvd_last_error(jsvd_ctx_t ctx);
+const char *jsvd_status_string(int status);
+
+/* One-sided Jacobi SVD  A = U diag(S) V^T  (Sec. 2, Eqs. (2.3)-(2.9); Sec. 4).
+ *   m, n  : m >= n >= 1 (a wider matrix must be passed transposed: -2)
+ *   A     : device, m x n, lda >= m; read only
+ *   S     : device, n singular values (non-increasing when opts->sort)
+ *   U     : device, m x n (ldu >= m), left singular vectors (u_i = g_i / s_i,
+ *           a zero column where s_i = 0)
+ *   V     : device, n x n (ldv >= n), right singular vectors; may be NULL
+ *   opts  : may be NULL (defaults); info: may be NULL.
+ * n that is not a multiple of 2b is bordered internally with an identity
+ * block; the border never appears in the outputs.                          */
+int jsvd_dgesvj(jsvd_ctx_t ctx, int m, int n, const double *A, int lda,
+                double *S, double *U, int ldu, double *V, int ldv,
+                const jsvd_opts *opts, jsvd_info *info);
+
+/* Hyperbolic SVD  G = U diag(S) V^T  with  V^T J V = J,
+ * J = diag(+1 x n_plus, -1 x (n - n_plus))  (Eq. (2.10); Sec. 4).
+ * Pairs of columns k <= n_plus < l are rotated hyperbolically (Eq. (4.2)),
+ * the others trigonometrically; only trigonometric pairs are sorted, so S is
+ * non-increasing inside each sign block.  Arguments as for jsvd_dgesvj;
+ * 0 <= n_plus <= n.  n_plus = n gives exactly jsvd_dgesvj.                 */
+int jsvd_dhsvj(jsvd_ctx_t ctx, int m, int n, int n_plus, const double *G, int ldg,
+               double *S, double *U, int ldu, double *V, int ldv,
+               const jsvd_opts *opts, jsvd_info *info);
+
+/* The block p-strategy table of order nblocks (even, >= 2) for `strategy`:
+ * out_pairs (host, 2*(nblocks-1)*(nblocks/2) ints) receives, p-step by p-step,
+ * the 0-based pairs (p, q), p < q.  The R/C families need nblocks = 2^k * o
+ * with 2o <= 24 (Alg. 3.1 is run at order 2o, Alg. 3.2 expands it).
+ * Host only; needs no GPU.                                                  */
+int jsvd_pivot_table(int strategy, int nblocks, int *out_pairs);
+
+/* Rotation parameters of Eqs. (4.3)-(4.6) (cs_2 form) evaluated on the GPU
+ * by the same device code the sweep kernels use.  All arrays are device
+ * memory of length count; hyperbolic[i] != 0 selects Eq. (4.2).  proper[i]
+ * = 1 if cs != 1.  Exposed so that the rotation arithmetic can be compared
+ * bit for bit with an independent CPU evaluation.                          */
+int jsvd_rotation_params(jsvd_ctx_t ctx, int count, const double *hpp,
+                         const double *hqq, const double *hpq,
+                         const int *hyperbolic, double *cs, double *tn,
+                         int *proper);
+
+/* ---- instrumentation ---------------------------------------------------
+ * Kernel classes: 0 = Gram partials, 1 = per-pair Cholesky + inner sweep,
+ * 2 = block update (Eq. (2.9)), 3 = everything else (bordering copy, V = I,
+ * column norms, output assembly, mixed-precision and batched kernels).
+ * jsvd_profile(ctx, 1) clears the tallies and starts timing: every launch of
+ * a class-0..2 kernel is then bracketed by CUDA events recorded on the
+ * context's stream and the elapsed times are summed at each sweep boundary.
+ * Launch counts and algorithmic FLOP counts are tallied whether or not
+ * timing is on (cleared by jsvd_profile).  jsvd_profile_read copies ms[i],
+ * launches[i] and flops[i] for i < nclass (nclass <= 4); any pointer may be
+ * NULL.  Algorithmic FLOPs per pivot block pair with bb = 2b: Gram
+ * m*bb*(bb+1), inner sweep 9*bb*bb*(bb-1) + bb^3/3, update 2*(m+n)*bb*bb
+ * (only pairs with V' != I), with the caller's m and n.                     */
+int jsvd_profile(jsvd_ctx_t ctx, int enable);
+int jsvd_profile_read(jsvd_ctx_t ctx, double *ms, long long *launches, double *flops, int nclass);
+
+/* FP64 throughput of this GPU, measured now: a DFMA-chain kernel and an FP64
+ * mma.sync (m8n8k4) kernel, each filling every SM for about `seconds`
+ * (0 < seconds <= 60) after a warm-up of the same length, timed with CUDA
+ * events on the context's stream.  Results in TFLOP/s (2 per FMA); either
+ * pointer may be NULL.  Allocates and frees a small scratch buffer.        */
+int jsvd_fp64_peak(jsvd_ctx_t ctx, double seconds, double *dfma_tflops, double *dmma_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JSVD_H */

@@ -1,0 +1,524 @@
+// Host driver and C ABI (include/jsvd.h): context and workspace, bordering,
+// the block-sweep loop with the GPU-wide stopping rule (Sec. 4.5), singular
+// value extraction (kernel Sigma, Sec. 4) and the final ordering.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "jsvd.h"
+#include "jsvd_internal.h"
+#include "driver.h"
+#include "rotation.cuh"
+#include "sweep_fp64.cuh"
+
+using namespace jsvd;
+
+// ---------------------------------------------------------------------------
+// small kernels: bordering copy, V = I, norms, output assembly
+
+// Workspace column c of the bordered matrix: real columns keep their order;
+// the k border columns sit at [ins, ins + k) and carry a 1 in row m + (c-ins).
+__global__ void k_init_g(const double *__restrict__ A, int lda, int m, int n, int ins, int k,
+                         double *__restrict__ G, int ldg, int g_rows, int n_pad,
+                         unsigned long long *err) {
+    const size_t total = (size_t)g_rows * n_pad;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % g_rows), c = (int)(e / g_rows);
+        double v = 0.0;
+        if (c >= ins && c < ins + k) {
+            v = (r == m + (c - ins)) ? 1.0 : 0.0;
+        } else if (r < m) {
+            const int src = c < ins ? c : c - k;
+            v = A[(size_t)src * lda + r];
+            if (!isfinite(v)) atomicOr(err, 1ull);
+        }
+        G[(size_t)c * ldg + r] = v;
+    }
+}
+
+__global__ void k_eye(double *__restrict__ V, int ldv, int v_rows, int n_pad) {
+    const size_t total = (size_t)v_rows * n_pad;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % v_rows), c = (int)(e / v_rows);
+        V[(size_t)c * ldv + r] = (r == c) ? 1.0 : 0.0;
+    }
+}
+
+// sigma_c = ||g_c||_2 (one warp per column, lane-strided sums then a fixed
+// shuffle tree); border[c] = 1 if column c has support in the border rows.
+__global__ void k_colnorms(const double *__restrict__ G, int ldg, int rows, int m, int k,
+                           int n_pad, double *__restrict__ sigma, int *__restrict__ border) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (warp >= n_pad) return;
+    const double *g = G + (size_t)warp * ldg;
+    double s = 0.0;
+    int bd = 0;
+    for (int r = lane; r < rows; r += 32) {
+        const double x = g[r];
+        s = __fma_rn(x, x, s);
+        if (r >= m && r < m + k && x != 0.0) bd = 1;
+    }
+    for (int off = 16; off > 0; off >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off));
+    bd = __any_sync(0xffffffffu, bd);
+    if (lane == 0) {
+        sigma[warp] = __dsqrt_rn(s);
+        border[warp] = bd;
+    }
+}
+
+// Output column i takes workspace column perm[i]:
+//   U(:, i) = g / sigma (zero column if sigma = 0), S(i) = sigma,
+//   V(r, i) = js(r) * W(row(r), perm[i]) * js(i)   (V = J W J for the HSVD).
+__global__ void k_finalize(const double *__restrict__ G, int ldg, const double *__restrict__ W,
+                           int ldw, const double *__restrict__ sigma, const int *__restrict__ perm,
+                           int m, int n, int ins, int k, int nplus, int hyperbolic,
+                           double *__restrict__ S, double *__restrict__ U, int ldu,
+                           double *__restrict__ Vo, int ldv) {
+    const int i = blockIdx.y;
+    const int c = perm[i];
+    const double sg = sigma[c];
+    if (blockIdx.x == 0 && threadIdx.x == 0) S[i] = sg;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        const double g = G[(size_t)c * ldg + r];
+        U[(size_t)i * ldu + r] = sg > 0.0 ? __ddiv_rn(g, sg) : 0.0;
+    }
+    if (Vo) {
+        const double ji = (i < nplus) ? 1.0 : -1.0;
+        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+            const int rw = r < ins ? r : r + k;
+            double v = W[(size_t)c * ldw + rw];
+            if (hyperbolic) {
+                const double jr = (r < nplus) ? 1.0 : -1.0;
+                v = v * jr * ji;
+            }
+            Vo[(size_t)i * ldv + r] = v;
+        }
+    }
+}
+
+__global__ void k_rot_params(int count, const double *hpp, const double *hqq, const double *hpq,
+                             const int *hyp, double *cs, double *tn, int *proper) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const Rot r = rot_params(hpp[i], hqq[i], hpq[i], hyp[i] ? -1.0 : 1.0);
+    cs[i] = r.cs;
+    tn[i] = r.tn;
+    proper[i] = r.cs != 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// context
+
+void jsvd_ctx::set_error(const char *where, cudaError_t e) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+    last_error = buf;
+}
+
+int jsvd_ctx::check(const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(where, e);
+        return JSVD_ERR_CUDA;
+    }
+    return 0;
+}
+
+int jsvd_ctx::ensure(Buffer &buf, size_t bytes) {
+    if (buf.bytes >= bytes) return 0;
+    if (buf.ptr) cudaFree(buf.ptr);
+    buf.ptr = nullptr;
+    buf.bytes = 0;
+    cudaError_t e = cudaMalloc(&buf.ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc", e);
+        return JSVD_ERR_ALLOC;
+    }
+    buf.bytes = bytes;
+    return 0;
+}
+
+int jsvd_ctx::table(int strategy, int n, const int **dev) {
+    auto key = std::make_pair(strategy, n);
+    auto it = tables.find(key);
+    if (it == tables.end()) {
+        std::vector<int> t;
+        int rc = build_pstrategy(strategy, n, t);
+        if (rc) {
+            last_error = "no pivot table of order " + std::to_string(n) + " for this strategy";
+            return JSVD_ERR_UNSUPPORTED;
+        }
+        Buffer b;
+        if (int r2 = ensure(b, t.size() * sizeof(int))) return r2;
+        cudaMemcpyAsync(b.ptr, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, stream);
+        if (int r3 = check("table upload")) return r3;
+        it = tables.emplace(key, b).first;
+        host_tables[key] = t;
+    }
+    *dev = (const int *)it->second.ptr;
+    return 0;
+}
+
+int jsvd_ctx::inner_table(int strategy, int BB, const unsigned char **dev) {
+    auto key = std::make_pair(strategy, -BB);
+    auto it = tables.find(key);
+    if (it == tables.end()) {
+        std::vector<int> t;
+        int rc = build_pstrategy(strategy, BB, t);
+        if (rc) {
+            last_error = "no inner pivot table of order " + std::to_string(BB);
+            return JSVD_ERR_UNSUPPORTED;
+        }
+        std::vector<unsigned char> u(t.begin(), t.end());
+        Buffer b;
+        if (int r2 = ensure(b, u.size())) return r2;
+        cudaMemcpy(b.ptr, u.data(), u.size(), cudaMemcpyHostToDevice);
+        if (int r3 = check("inner table upload")) return r3;
+        it = tables.emplace(key, b).first;
+    }
+    *dev = (const unsigned char *)it->second.ptr;
+    return 0;
+}
+
+jsvd_ctx::~jsvd_ctx() {
+    for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm})
+        if (b->ptr) cudaFree(b->ptr);
+    for (auto &kv : tables)
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    if (host_counters) cudaFreeHost(host_counters);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+}
+
+int jsvd_ctx::ensure_events(size_t count) {
+    while (events.size() < count) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return check("cudaEventCreate");
+        events.push_back(e);
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// the solver
+
+namespace {
+
+int choose_b(const jsvd_opts &o, int n) {
+    if (o.b) return o.b;
+    if (n >= 1024) return 32;
+    if (n >= 96) return 16;
+    return 8;
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double *S, double *U,
+                    int ldu, double *Vout, int ldv, const jsvd_opts *opts_in, jsvd_info *info,
+                    bool hyperbolic) {
+    jsvd_opts o;
+    jsvd_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if (o.max_sweeps <= 0) o.max_sweeps = 30;
+    if (o.inner_sweeps <= 0) o.inner_sweeps = 1;
+    if (o.inner_strategy < 0) o.inner_strategy = o.strategy;
+    if (o.strategy < 0 || o.strategy > 4 || o.inner_strategy > 4) return JSVD_ERR_UNSUPPORTED;
+    if (o.precision != JSVD_PREC_FP64) {
+        last_error = "precision mode not available in this entry point";
+        return JSVD_ERR_UNSUPPORTED;
+    }
+    const int b = choose_b(o, n);
+    if (b != 8 && b != 16 && b != 32) {
+        last_error = "block width must be 8, 16 or 32";
+        return JSVD_ERR_UNSUPPORTED;
+    }
+    const int BB = 2 * b;
+    const int nplus = hyperbolic ? nplus_in : n;
+
+    // bordering: n_pad = b * n_b with n_b even and admissible for the strategy
+    int nb = (int)((n + b - 1) / b);
+    nb = admissible_order(o.strategy, nb < 2 ? 2 : nb);
+    const int n_pad = nb * b;
+    const int k = n_pad - n;
+    const int ins = nplus;                    // border inserted at the J boundary
+    const int nplus_w = nplus + k;            // border columns are J = +1
+    const int m_b = m + k;
+    const int g_rows = (int)round_up(m_b, kRowAlign);
+    const int v_rows = (int)round_up(n_pad, kRowAlign);
+    const int npairs = nb / 2;
+    const int g_chunks = g_rows / kGramRows;
+
+    int rc;
+    if ((rc = ensure(g, sizeof(double) * (size_t)g_rows * n_pad))) return rc;
+    if ((rc = ensure(v, sizeof(double) * (size_t)v_rows * n_pad))) return rc;
+    if ((rc = ensure(part, sizeof(double) * (size_t)npairs * g_chunks * (BB * (BB + 1) / 2)))) return rc;
+    if ((rc = ensure(vprime, sizeof(double) * (size_t)npairs * BB * BB))) return rc;
+    if ((rc = ensure(vflag, sizeof(int) * (size_t)npairs))) return rc;
+    if ((rc = ensure(counters, sizeof(unsigned long long) * kCntSize))) return rc;
+    if ((rc = ensure(sigma, sizeof(double) * (size_t)n_pad))) return rc;
+    if ((rc = ensure(border, sizeof(int) * (size_t)n_pad))) return rc;
+    if ((rc = ensure(perm, sizeof(int) * (size_t)n_pad))) return rc;
+    if (!host_counters) {
+        if (cudaMallocHost(&host_counters, sizeof(unsigned long long) * kCntSize) != cudaSuccess) {
+            cudaGetLastError();
+            return JSVD_ERR_ALLOC;
+        }
+    }
+    const int *dtab = nullptr;
+    const unsigned char *dinner = nullptr;
+    if ((rc = table(o.strategy, nb, &dtab))) return rc;
+    if ((rc = inner_table(o.inner_strategy, BB, &dinner))) return rc;
+
+    double *G = (double *)g.ptr, *V = (double *)v.ptr;
+    unsigned long long *cnt = (unsigned long long *)counters.ptr;
+
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
+    k_init_g<<<1024, 256, 0, stream>>>(A, lda, m, n, ins, k, G, g_rows, g_rows, n_pad, cnt + kCntErr);
+    k_eye<<<1024, 256, 0, stream>>>(V, v_rows, v_rows, n_pad);
+    prof_launches[3] += 2;
+    if (profiling && (rc = ensure_events(4 * (size_t)(nb - 1)))) return rc;
+    const double bbd = (double)BB;
+    const double fl_gram = (double)npairs * m * bbd * (bbd + 1.0);
+    const double fl_jac = (double)npairs * (9.0 * bbd * bbd * (bbd - 1.0) + bbd * bbd * bbd / 3.0);
+    const double fl_upd_pair = 2.0 * ((double)m + (Vout ? (double)n : 0.0)) * bbd * bbd;
+    if ((rc = check("init"))) return rc;
+    cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize, cudaMemcpyDeviceToHost, stream);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return check("init sync") ? JSVD_ERR_CUDA : JSVD_ERR_CUDA;
+    if (host_counters[kCntErr]) {
+        last_error = "input holds Inf or NaN";
+        return JSVD_ERR_NONFINITE;
+    }
+
+    PStepArgs a{};
+    a.G = G; a.ldg = g_rows; a.g_rows = g_rows;
+    a.V = V; a.ldv = v_rows; a.v_rows = v_rows;
+    a.table = dtab; a.npairs = npairs; a.inner = dinner;
+    a.b = b; a.nplus = nplus_w; a.inner_sweeps = o.inner_sweeps;
+    a.part = (double *)part.ptr; a.g_chunks = g_chunks;
+    a.vprime = (double *)vprime.ptr; a.vflag = (int *)vflag.ptr;
+    a.counters = cnt;
+
+    jsvd_info inf{};
+    inf.b = b;
+    int converged = 0, sweeps = 0;
+    for (sweeps = 0; sweeps < o.max_sweeps;) {
+        cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
+        for (int s = 0; s < nb - 1; ++s) {
+            a.step = s;
+            launch_pstep_fp64(BB, a, stream, profiling ? &events[4 * (size_t)s] : nullptr);
+        }
+        prof_launches[0] += nb - 1;
+        prof_launches[1] += nb - 1;
+        prof_launches[2] += nb - 1;
+        if ((rc = check("p-step"))) return rc;
+        cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize,
+                        cudaMemcpyDeviceToHost, stream);
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) { set_error("sweep", e); return JSVD_ERR_CUDA; }
+        ++sweeps;
+        prof_flops[0] += fl_gram * (nb - 1);
+        prof_flops[1] += fl_jac * (nb - 1);
+        prof_flops[2] += fl_upd_pair * (double)host_counters[kCntUpdated];
+        if (profiling) {
+            for (int s = 0; s < nb - 1; ++s)
+                for (int c = 0; c < 3; ++c) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, events[4 * (size_t)s + c], events[4 * (size_t)s + c + 1]);
+                    prof_ms[c] += ms;
+                }
+        }
+        inf.rotations += (long long)host_counters[kCntRot];
+        inf.proper_rotations += (long long)host_counters[kCntProper];
+        inf.pairs_updated += (long long)host_counters[kCntUpdated];
+        inf.breakdowns += (long long)host_counters[kCntBreak];
+        double off;
+        unsigned long long bits = host_counters[kCntOff];
+        memcpy(&off, &bits, sizeof off);
+        inf.off_norm = off;
+        if (verbose)
+            fprintf(stderr, "[jsvd] sweep %d: rotations %llu proper %llu updated %llu off %.3e\n", sweeps,
+                    host_counters[kCntRot], host_counters[kCntProper], host_counters[kCntUpdated], off);
+        if (host_counters[kCntProper] == 0) { converged = 1; break; }
+    }
+    inf.sweeps = sweeps;
+    inf.converged = converged;
+
+    // kernel Sigma: column norms, border detection, ordering, outputs
+    double *dsig = (double *)sigma.ptr;
+    int *dbd = (int *)border.ptr;
+    k_colnorms<<<(n_pad * 32 + 255) / 256, 256, 0, stream>>>(G, g_rows, m_b, m, k, n_pad, dsig, dbd);
+    prof_launches[3] += 2;  // column norms and output assembly
+    if ((rc = check("colnorms"))) return rc;
+    std::vector<double> hs(n_pad);
+    std::vector<int> hb(n_pad);
+    cudaMemcpyAsync(hs.data(), dsig, sizeof(double) * n_pad, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(hb.data(), dbd, sizeof(int) * n_pad, cudaMemcpyDeviceToHost, stream);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return check("sigma sync") ? JSVD_ERR_CUDA : JSVD_ERR_CUDA;
+    std::vector<int> pos, neg;
+    for (int c = 0; c < n_pad; ++c) {
+        if (hb[c]) continue;
+        (c < nplus_w ? pos : neg).push_back(c);
+    }
+    if ((int)(pos.size() + neg.size()) != n) {
+        last_error = "border columns could not be separated from the matrix columns";
+        return JSVD_ERR_CUDA;
+    }
+    if (o.sort) {
+        auto desc = [&](int x, int y) { return hs[x] > hs[y]; };
+        std::stable_sort(pos.begin(), pos.end(), desc);
+        std::stable_sort(neg.begin(), neg.end(), desc);
+    }
+    std::vector<int> hp(pos);
+    hp.insert(hp.end(), neg.begin(), neg.end());
+    cudaMemcpyAsync(perm.ptr, hp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+    dim3 grid((std::max(m, n) + 255) / 256 < 8 ? (std::max(m, n) + 255) / 256 : 8, n);
+    k_finalize<<<grid, 256, 0, stream>>>(G, g_rows, V, v_rows, dsig, (int *)perm.ptr, m, n, ins, k,
+                                         nplus, hyperbolic ? 1 : 0, S, U, ldu, Vout, ldv);
+    if ((rc = check("finalize"))) return rc;
+    // the host vector hp must outlive the async copy
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return check("final sync") ? JSVD_ERR_CUDA : JSVD_ERR_CUDA;
+    if (info) *info = inf;
+    return converged ? JSVD_SUCCESS : JSVD_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+void jsvd_default_opts(jsvd_opts *o) {
+    if (!o) return;
+    o->b = 0;
+    o->strategy = JSVD_STRAT_ROW_REV;
+    o->inner_strategy = -1;
+    o->inner_sweeps = 1;
+    o->max_sweeps = 30;
+    o->precision = JSVD_PREC_FP64;
+    o->sort = 1;
+}
+
+int jsvd_create(jsvd_ctx_t *ctx, int device, void *stream) {
+    if (!ctx) return -1;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return -2;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return JSVD_ERR_CUDA; }
+    jsvd_ctx *c = new jsvd_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    const char *v = getenv("JSVD_VERBOSE");
+    c->verbose = v && *v && *v != '0';
+    *ctx = c;
+    return 0;
+}
+
+int jsvd_destroy(jsvd_ctx_t ctx) {
+    if (!ctx) return -1;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return 0;
+}
+
+int jsvd_set_stream(jsvd_ctx_t ctx, void *stream) {
+    if (!ctx) return -1;
+    ctx->stream = (cudaStream_t)stream;
+    return 0;
+}
+
+int jsvd_profile(jsvd_ctx_t ctx, int enable) {
+    if (!ctx) return -1;
+    ctx->profiling = enable != 0;
+    for (int i = 0; i < 4; ++i) {
+        ctx->prof_ms[i] = 0.0;
+        ctx->prof_launches[i] = 0;
+        ctx->prof_flops[i] = 0.0;
+    }
+    return 0;
+}
+
+int jsvd_profile_read(jsvd_ctx_t ctx, double *ms, long long *launches, double *flops, int nclass) {
+    if (!ctx) return -1;
+    if (nclass < 0 || nclass > 4) return -5;
+    for (int i = 0; i < nclass; ++i) {
+        if (ms) ms[i] = ctx->prof_ms[i];
+        if (launches) launches[i] = ctx->prof_launches[i];
+        if (flops) flops[i] = ctx->prof_flops[i];
+    }
+    return 0;
+}
+
+const char *jsvd_last_error(jsvd_ctx_t ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+const char *jsvd_status_string(int s) {
+    switch (s) {
+        case JSVD_SUCCESS: return "success";
+        case JSVD_NOT_CONVERGED: return "sweep limit reached before convergence";
+        case JSVD_ERR_NONFINITE: return "input holds Inf or NaN";
+        case JSVD_ERR_CUDA: return "CUDA error";
+        case JSVD_ERR_ALLOC: return "workspace allocation failed";
+        case JSVD_ERR_UNSUPPORTED: return "unsupported option";
+        case JSVD_ERR_TIMEOUT: return "bounded device wait gave up";
+        default: return s < 0 ? "invalid argument" : "unknown status";
+    }
+}
+
+int jsvd_dgesvj(jsvd_ctx_t ctx, int m, int n, const double *A, int lda, double *S, double *U,
+                int ldu, double *V, int ldv, const jsvd_opts *opts, jsvd_info *info) {
+    if (!ctx) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1) return -3;
+    if (!A) return -4;
+    if (lda < m) return -5;
+    if (!S) return -6;
+    if (!U) return -7;
+    if (ldu < m) return -8;
+    if (V && ldv < n) return -10;
+    cudaSetDevice(ctx->device);
+    return ctx->solve(m, n, n, A, lda, S, U, ldu, V, ldv, opts, info, false);
+}
+
+int jsvd_dhsvj(jsvd_ctx_t ctx, int m, int n, int n_plus, const double *G, int ldg, double *S,
+               double *U, int ldu, double *V, int ldv, const jsvd_opts *opts, jsvd_info *info) {
+    if (!ctx) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1) return -3;
+    if (n_plus < 0 || n_plus > n) return -4;
+    if (!G) return -5;
+    if (ldg < m) return -6;
+    if (!S) return -7;
+    if (!U) return -8;
+    if (ldu < m) return -9;
+    if (V && ldv < n) return -11;
+    cudaSetDevice(ctx->device);
+    return ctx->solve(m, n, n_plus, G, ldg, S, U, ldu, V, ldv, opts, info, n_plus < n);
+}
+
+int jsvd_rotation_params(jsvd_ctx_t ctx, int count, const double *hpp, const double *hqq,
+                         const double *hpq, const int *hyperbolic, double *cs, double *tn,
+                         int *proper) {
+    if (!ctx) return -1;
+    if (count < 0) return -2;
+    if (count == 0) return 0;
+    cudaSetDevice(ctx->device);
+    k_rot_params<<<(count + 255) / 256, 256, 0, ctx->stream>>>(count, hpp, hqq, hpq, hyperbolic, cs, tn, proper);
+    if (int rc = ctx->check("rotation params")) return rc;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ctx->check("rotation sync") ? JSVD_ERR_CUDA : JSVD_ERR_CUDA;
+    return 0;
+}
+
+}  // extern "C"

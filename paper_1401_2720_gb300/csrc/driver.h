@@ -1,0 +1,45 @@
+// The context object behind jsvd_ctx_t.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "jsvd.h"
+
+struct Buffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct jsvd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool verbose = false;
+    std::string last_error;
+
+    // workspace (grown on demand, freed with the context)
+    Buffer g, v, part, vprime, vflag, counters, sigma, border, perm;
+    unsigned long long *host_counters = nullptr;  // pinned
+    std::map<std::pair<int, int>, Buffer> tables;  // (strategy, order) -> device table
+    std::map<std::pair<int, int>, std::vector<int>> host_tables;
+
+    // instrumentation (jsvd_profile)
+    bool profiling = false;
+    double prof_ms[4] = {0, 0, 0, 0};
+    long long prof_launches[4] = {0, 0, 0, 0};
+    double prof_flops[4] = {0, 0, 0, 0};
+    std::vector<cudaEvent_t> events;  // 4 per p-step of one sweep
+    int ensure_events(size_t count);
+
+    ~jsvd_ctx();
+    void set_error(const char *where, cudaError_t e);
+    int check(const char *where);
+    int ensure(Buffer &buf, size_t bytes);
+    int table(int strategy, int n, const int **dev);
+    int inner_table(int strategy, int BB, const unsigned char **dev);
+    int solve(int m, int n, int nplus, const double *A, int lda, double *S, double *U, int ldu,
+              double *V, int ldv, const jsvd_opts *opts, jsvd_info *info, bool hyperbolic);
+};

@@ -1,0 +1,93 @@
+// FP64 throughput probe: the denominator of the roofline fraction the
+// benchmark reports.  Two kernels keep every SM's FP64 pipe busy for a
+// requested time, one with independent DFMA chains and one with FP64
+// mma.sync (m8n8k4) accumulations; both are timed with CUDA events on the
+// context's stream after a warm-up of the same length (so the SM clock has
+// settled).  Nothing here is on the SVD path.
+#include <cuda_runtime.h>
+
+#include "driver.h"
+#include "jsvd.h"
+
+namespace {
+
+constexpr int kChains = 8;
+
+__global__ void probe_dfma(double *out, int iters) {
+    double a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = 1e-3 * threadIdx.x + j;
+    const double b = 0.9999999, c = 1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int j = 0; j < kChains; ++j) a[j] = __fma_rn(a[j], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void probe_dmma(double *out, int iters) {
+    const double a = 1e-3 * (threadIdx.x & 7), b = 0.5;
+    double c[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                         : "+d"(c[j][0]), "+d"(c[j][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += c[j][0] + c[j][1];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" int jsvd_fp64_peak(jsvd_ctx_t ctx, double seconds, double *dfma_tflops, double *dmma_tflops) {
+    if (!ctx) return -1;
+    if (!(seconds > 0.0) || seconds > 60.0) return -2;
+    cudaSetDevice(ctx->device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const int blocks = sms * 4, threads = 256;
+    double *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(double) * blocks * threads) != cudaSuccess) return ctx->check("probe alloc");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = 0;
+    for (int kind = 0; kind < 2 && !rc; ++kind) {
+        // calibrate the iteration count on a short launch, then warm up and time
+        int iters = 64;
+        float ms = 0.f;
+        for (int pass = 0; pass < 3; ++pass) {
+            cudaEventRecord(e0, ctx->stream);
+            if (kind == 0) probe_dfma<<<blocks, threads, 0, ctx->stream>>>(buf, iters);
+            else probe_dmma<<<blocks, threads, 0, ctx->stream>>>(buf, iters);
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = ctx->check("probe"); break; }
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pass < 2) {
+                double scale = (seconds * 1e3) / (ms > 1e-3 ? ms : 1e-3);
+                double next = iters * scale;
+                iters = next > 2e9 ? 2000000000 : (next < 1 ? 1 : (int)next);
+            }
+        }
+        if (rc) break;
+        const double fl = kind == 0 ? 2.0 * kChains * 8 * (double)iters * blocks * threads
+                                    : 2.0 * 8 * 8 * 4 * 4 * (double)iters * blocks * (threads / 32);
+        const double tf = fl / (ms * 1e-3) / 1e12;
+        if (kind == 0 && dfma_tflops) *dfma_tflops = tf;
+        if (kind == 1 && dmma_tflops) *dmma_tflops = tf;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (!rc) rc = ctx->check("probe");
+    return rc;
+}

@@ -1,0 +1,235 @@
+"""Python binding of the C ABI in include/jsvd.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library libjsvd.so built by
+``paper_1401_2720_gb300.build_ext``; there is no CPU fallback.  If the
+library is missing the calls raise.
+
+Tensors are torch.float64 CUDA tensors.  The library is column-major; a
+torch (row-major) m x n tensor is handed over as the column-major buffer of
+its transpose, and results come back as column-major views.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libjsvd.so")
+
+STRATEGIES = {"modulus": 0, "R": 1, "C": 2, "rR": 3, "rC": 4}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+STATUS = {0: "success", 1: "not converged", 2: "non-finite input", 3: "CUDA error",
+          4: "allocation failed", 5: "unsupported", 6: "device wait timed out"}
+
+
+class JsvdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"jsvd status {status} ({STATUS.get(status, 'invalid argument')}): {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_int), ("strategy", ctypes.c_int), ("inner_strategy", ctypes.c_int),
+                ("inner_sweeps", ctypes.c_int), ("max_sweeps", ctypes.c_int),
+                ("precision", ctypes.c_int), ("sort", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("sweeps_low", ctypes.c_int), ("converged", ctypes.c_int),
+                ("b", ctypes.c_int), ("rotations", ctypes.c_longlong),
+                ("proper_rotations", ctypes.c_longlong), ("pairs_updated", ctypes.c_longlong),
+                ("breakdowns", ctypes.c_longlong), ("off_norm", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+_ctx: dict[int, ctypes.c_void_p] = {}
+
+EXPORTED = ["jsvd_default_opts", "jsvd_create", "jsvd_destroy", "jsvd_set_stream",
+            "jsvd_last_error", "jsvd_status_string", "jsvd_dgesvj", "jsvd_dhsvj",
+            "jsvd_pivot_table", "jsvd_rotation_params", "jsvd_profile", "jsvd_profile_read",
+            "jsvd_fp64_peak"]
+
+
+def library():
+    """Load libjsvd.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_1401_2720_gb300.build_ext.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            lib.jsvd_default_opts.argtypes = [ctypes.POINTER(Opts)]
+            lib.jsvd_default_opts.restype = None
+            lib.jsvd_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I, P]
+            lib.jsvd_destroy.argtypes = [P]
+            lib.jsvd_set_stream.argtypes = [P, P]
+            lib.jsvd_last_error.argtypes = [P]
+            lib.jsvd_last_error.restype = ctypes.c_char_p
+            lib.jsvd_status_string.argtypes = [I]
+            lib.jsvd_status_string.restype = ctypes.c_char_p
+            lib.jsvd_dgesvj.argtypes = [P, I, I, P, I, P, P, I, P, I, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+            lib.jsvd_dhsvj.argtypes = [P, I, I, I, P, I, P, P, I, P, I, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+            lib.jsvd_pivot_table.argtypes = [I, I, P]
+            lib.jsvd_rotation_params.argtypes = [P, I, P, P, P, P, P, P, P]
+            lib.jsvd_profile.argtypes = [P, I]
+            lib.jsvd_profile_read.argtypes = [P, P, P, P, I]
+            lib.jsvd_fp64_peak.argtypes = [P, D, P, P]
+            _lib = lib
+    return _lib
+
+
+def context(device: int | None = None) -> ctypes.c_void_p:
+    """The per-device library context, bound to torch's current stream."""
+    lib = library()
+    dev = torch.cuda.current_device() if device is None else int(device)
+    with _lock:
+        if dev not in _ctx:
+            h = ctypes.c_void_p()
+            rc = lib.jsvd_create(ctypes.byref(h), dev, None)
+            if rc:
+                raise JsvdError(rc, "jsvd_create failed")
+            _ctx[dev] = h
+    h = _ctx[dev]
+    lib.jsvd_set_stream(h, ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+    return h
+
+
+def _raise(rc: int, h) -> None:
+    msg = library().jsvd_last_error(h).decode() if h else ""
+    raise JsvdError(rc, msg)
+
+
+def make_opts(b: int = 0, strategy: str = "rR", inner_strategy: str | None = None,
+              inner_sweeps: int = 1, max_sweeps: int = 30, precision: str = "fp64",
+              sort: bool = True) -> Opts:
+    o = Opts()
+    library().jsvd_default_opts(ctypes.byref(o))
+    o.b = b
+    o.strategy = STRATEGIES[strategy]
+    o.inner_strategy = -1 if inner_strategy is None else STRATEGIES[inner_strategy]
+    o.inner_sweeps = inner_sweeps
+    o.max_sweeps = max_sweeps
+    o.precision = PRECISIONS[precision]
+    o.sort = 1 if sort else 0
+    return o
+
+
+def _colmajor(A: torch.Tensor) -> tuple[torch.Tensor, int]:
+    """(buffer, ld) of A as a column-major matrix."""
+    if A.dtype != torch.float64 or not A.is_cuda or A.dim() != 2:
+        raise ValueError("expected a 2-D torch.float64 CUDA tensor")
+    m = A.shape[0]
+    if A.stride(0) == 1 and A.stride(1) >= max(m, 1):
+        return A, A.stride(1)
+    return A.t().contiguous().t(), m
+
+
+def _outputs(m: int, n: int, with_v: bool, device):
+    U = torch.empty((n, m), dtype=torch.float64, device=device).t()
+    S = torch.empty(n, dtype=torch.float64, device=device)
+    V = torch.empty((n, n), dtype=torch.float64, device=device).t() if with_v else None
+    return U, S, V
+
+
+def svd(A: torch.Tensor, *, with_v: bool = True, return_info: bool = False, out=None, **kw):
+    """A = U diag(S) V^T by the block-oriented one-sided Jacobi method.
+    A: m x n (m >= n) float64 CUDA tensor.  Keyword options as in make_opts."""
+    m, n = A.shape
+    if m < n:
+        raise ValueError("svd needs m >= n; pass A.T")
+    Ac, lda = _colmajor(A)
+    U, S, V = out if out is not None else _outputs(m, n, with_v, A.device)
+    opts = make_opts(**kw)
+    info = Info()
+    h = context(A.device.index)
+    rc = library().jsvd_dgesvj(h, m, n, Ac.data_ptr(), lda, S.data_ptr(), U.data_ptr(), U.stride(1),
+                               V.data_ptr() if V is not None else None, V.stride(1) if V is not None else 1,
+                               ctypes.byref(opts), ctypes.byref(info))
+    if rc not in (0, 1):
+        _raise(rc, h)
+    res = (U, S, V)
+    return (res + (dict(info.as_dict(), status=rc),)) if return_info else res
+
+
+def hsvd(G: torch.Tensor, n_plus: int, *, with_v: bool = True, return_info: bool = False, **kw):
+    """Hyperbolic SVD G = U diag(S) V^T, V^T J V = J, J = diag(I_{n_plus}, -I)."""
+    m, n = G.shape
+    if m < n:
+        raise ValueError("hsvd needs m >= n")
+    Gc, ldg = _colmajor(G)
+    U, S, V = _outputs(m, n, with_v, G.device)
+    opts = make_opts(**kw)
+    info = Info()
+    h = context(G.device.index)
+    rc = library().jsvd_dhsvj(h, m, n, int(n_plus), Gc.data_ptr(), ldg, S.data_ptr(), U.data_ptr(),
+                              U.stride(1), V.data_ptr() if V is not None else None,
+                              V.stride(1) if V is not None else 1, ctypes.byref(opts), ctypes.byref(info))
+    if rc not in (0, 1):
+        _raise(rc, h)
+    res = (U, S, V)
+    return (res + (dict(info.as_dict(), status=rc),)) if return_info else res
+
+
+def pivot_table(strategy: str, nblocks: int) -> np.ndarray:
+    """The library's p-strategy table, shape (nblocks-1, nblocks/2, 2), 0-based."""
+    out = np.zeros((nblocks - 1) * nblocks, dtype=np.int32)
+    rc = library().jsvd_pivot_table(STRATEGIES[strategy], nblocks, out.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise JsvdError(rc, f"no {strategy} table of order {nblocks}")
+    return out.reshape(nblocks - 1, nblocks // 2, 2)
+
+
+def rotation_params(hpp: torch.Tensor, hqq: torch.Tensor, hpq: torch.Tensor, hyperbolic: torch.Tensor):
+    """Eqs. (4.3)-(4.6) evaluated by the library's device code."""
+    n = hpp.numel()
+    dev = hpp.device
+    cs = torch.empty(n, dtype=torch.float64, device=dev)
+    tn = torch.empty(n, dtype=torch.float64, device=dev)
+    pr = torch.empty(n, dtype=torch.int32, device=dev)
+    hy = hyperbolic.to(device=dev, dtype=torch.int32).contiguous()
+    args = [t.contiguous() for t in (hpp, hqq, hpq)]
+    h = context(dev.index)
+    rc = library().jsvd_rotation_params(h, n, args[0].data_ptr(), args[1].data_ptr(), args[2].data_ptr(),
+                                        hy.data_ptr(), cs.data_ptr(), tn.data_ptr(), pr.data_ptr())
+    if rc:
+        _raise(rc, h)
+    return cs, tn, pr.bool()
+
+
+KERNEL_CLASSES = ("gram", "jacobi", "update", "other")
+
+
+def profile(enable: bool = True, device: int | None = None) -> None:
+    """Clear the library's kernel tallies; time the sweep kernels if enable."""
+    library().jsvd_profile(context(device), 1 if enable else 0)
+
+
+def profile_read(device: int | None = None) -> dict:
+    """{class: (milliseconds, launches, algorithmic flops)} since profile()."""
+    ms = np.zeros(4)
+    ln = np.zeros(4, dtype=np.int64)
+    fl = np.zeros(4)
+    library().jsvd_profile_read(context(device), ms.ctypes.data_as(ctypes.c_void_p),
+                                ln.ctypes.data_as(ctypes.c_void_p), fl.ctypes.data_as(ctypes.c_void_p), 4)
+    return {c: (float(ms[i]), int(ln[i]), float(fl[i])) for i, c in enumerate(KERNEL_CLASSES)}
+
+
+def fp64_peak(seconds: float = 1.0, device: int | None = None) -> tuple[float, float]:
+    """(DFMA, DMMA) FP64 TFLOP/s of this GPU measured by the library's probe."""
+    a = ctypes.c_double()
+    b = ctypes.c_double()
+    h = context(device)
+    rc = library().jsvd_fp64_peak(h, float(seconds), ctypes.byref(a), ctypes.byref(b))
+    if rc:
+        _raise(rc, h)
+    return a.value, b.value
