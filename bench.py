@@ -42,6 +42,11 @@ WORKLOADS = {
     "graded8192": (8192, 8192, "graded", "8192x8192 N(0,1), column j x 10^u_j, u_j~U(-4,0)"),
     "graded4096": (4096, 4096, "graded", "4096x4096 N(0,1), column j x 10^u_j, u_j~U(-4,0)"),
     "small512": (512, 256, "planted", "512x256 U diag(s) V^T, s geometric 1..1e-8, Haar U,V"),
+    "hsvd4096": (4096, 4096, "hsvd", "HSVD of 4096x4096 N(0,1), J=diag(+1 x2048, -1 x2048)"),
+    "mixed8192x4096": (8192, 4096, "mixed", "8192x4096 U diag(s) V^T, s_i=10^(-12 x_i), x~U(0,1), Haar U,V; "
+                                            "FP32 sweeps then FP64 sweeps"),
+    "mixed2048x1024": (2048, 1024, "mixed", "2048x1024 U diag(s) V^T, s_i=10^(-12 x_i), x~U(0,1), Haar U,V; "
+                                            "FP32 sweeps then FP64 sweeps"),
 }
 
 
@@ -64,6 +69,10 @@ def make_input(name: str, seed: int) -> np.ndarray:
     m, n, kind, _ = WORKLOADS[name]
     if kind == "graded":
         return inputs.graded_gaussian(m, n, seed)
+    if kind == "hsvd":
+        return inputs.gaussian(m, n, seed)
+    if kind == "mixed":
+        return inputs.workload_mixed(m, n, seed)[0]
     return inputs.planted(m, n, inputs.geometric(n, 1.0, 1e-8), seed)
 
 
@@ -115,7 +124,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_sample(A: np.ndarray, b: int, strategy: str, pairs: int, sweeps_hint: float):
+def cpu_sample(A: np.ndarray, b: int, strategy: str, pairs: int, sweeps_hint: float, nplus: int | None = None):
     """Time the oracle's block-oriented p-step on `pairs` pivot pairs of the
     full-size input and scale to s/matrix: (t / pairs) x pairs per sweep x sweeps."""
     import oracle
@@ -128,7 +137,7 @@ def cpu_sample(A: np.ndarray, b: int, strategy: str, pairs: int, sweeps_hint: fl
     V = np.asfortranarray(np.eye(n))
     step = tab[0][:pairs]
     t0 = time.perf_counter()
-    oracle.block_pstep(G, V, b, step, inner)
+    oracle.block_pstep(G, V, b, step, inner, nplus=nplus)
     t = time.perf_counter() - t0
     per_pair = t / len(step)
     pairs_per_sweep = (nb // 2) * (nb - 1)
@@ -146,7 +155,8 @@ def run_reference(args) -> None:
     vals = []
     sample = ""
     for i in range(args.warmup + args.steps):
-        v, sample = cpu_sample(A, args.b, args.strategy, args.cpu_pairs, args.cpu_sweeps)
+        nplus = A.shape[1] // 2 if WORKLOADS[args.workload][2] == "hsvd" else None
+        v, sample = cpu_sample(A, args.b, args.strategy, args.cpu_pairs, args.cpu_sweeps, nplus)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
@@ -159,6 +169,71 @@ def run_reference(args) -> None:
         "config": {"workload": desc, "b": args.b, "strategy": args.strategy},
         "cpu_baseline": {"value": value, "unit": "s/matrix", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "s/matrix", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args) -> None:
+    """Forward (one graph launch over all matrices) + backward (adjoint of
+    L = sum w_i s_i + <C, U V^T>, cotangents formed once outside the timed
+    region) of the 4096-matrix uneven batch."""
+    import torch
+
+    from paper_1401_2720_gb300 import build_ext, inputs
+    from paper_1401_2720_gb300 import jsvd as J
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    build_ext.build()
+    mats, sig, ws, Cs = inputs.workload_batch(args.batch, seed=args.seed)
+    pk = J.Packing([a.shape[0] for a in mats], [a.shape[1] for a in mats])
+    A = pk.pack(mats, dev)
+    b = args.b if args.b in (8, 16, 32) else None
+    U, S, V, infos, rc = J.svd_batched_packed(pk, A, b=b, return_info=True, max_sweeps=args.max_sweeps)
+    Us, Vs = pk.unpack_mn(U), pk.unpack_nn(V)
+    dU = torch.cat([torch.from_numpy(C).to(dev).mm(v).t().reshape(-1) for C, v in zip(Cs, Vs)])
+    dV = torch.cat([torch.from_numpy(C).to(dev).t().mm(u).t().reshape(-1) for C, u in zip(Cs, Us)])
+    dS = torch.cat([torch.from_numpy(w).to(dev) for w in ws])
+    for _ in range(args.warmup):
+        U, S, V = J.svd_batched_packed(pk, A, b=b, max_sweeps=args.max_sweeps)
+        J.svd_backward_packed(pk, U, S, V, dU, dS, dV)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    J.profile(True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    clocks.start()
+    fwd = bwd = 0.0
+    for _ in range(args.steps):
+        e[0].record(stream)
+        U, S, V, infos, rc = J.svd_batched_packed(pk, A, b=b, return_info=True, max_sweeps=args.max_sweeps)
+        e[1].record(stream)
+        dA = J.svd_backward_packed(pk, U, S, V, dU, dS, dV)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fwd += e[0].elapsed_time(e[1])
+        bwd += e[1].elapsed_time(e[2])
+    clk = clocks.stop()
+    prof = J.profile_read()
+    J.profile(False)
+    fwd /= args.steps
+    bwd /= args.steps
+    ms_step = fwd + bwd
+    flops = prof["other"][2] / args.steps
+    # accuracy spot check against the planted spectra (normwise per matrix)
+    err = max(float(np.max(np.abs(s.cpu().numpy() - st)) / st[0]) for s, st in zip(pk.unpack_n(S), sig))
+    line = {
+        "metric": METRIC, "value": ms_step / 1e3 / len(pk), "unit": "s/matrix", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {len(pk)} matrices, m~U{{16..512}}, n~U{{8..m}}, s log-uniform "
+                               f"[1e-6,1] with gaps >= 1e-3, Haar U,V; forward + adjoint backward",
+                   "b": "per-matrix default (8 for n<=256, else 16)" if b is None else b},
+        "matrices_per_s": len(pk) / (ms_step / 1e3),
+        "forward_ms": fwd, "backward_ms": bwd, "tflops": flops / (ms_step * 1e-3) / 1e12,
+        "sweeps_max": max(i["sweeps"] for i in infos), "sweeps_mean": statistics.mean(i["sweeps"] for i in infos),
+        "converged": all(i["converged"] for i in infos), "max_normwise_sigma_err_vs_planted": err,
+        "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
@@ -188,11 +263,19 @@ def run_gpu(args) -> None:
     U = torch.empty((n, m), dtype=torch.float64, device=dev).t()
     S = torch.empty(n, dtype=torch.float64, device=dev)
     V = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    kind = WORKLOADS[args.workload][2]
     kw = dict(b=args.b, strategy=args.strategy, max_sweeps=args.max_sweeps)
+    if kind == "mixed":
+        kw["precision"] = "mixed"
+
+    def solve(Ain):
+        if kind == "hsvd":
+            return J.hsvd(Ain, n // 2, out=(U, S, V), return_info=True, **kw)
+        return J.svd(Ain, out=(U, S, V), return_info=True, **kw)
 
     infos = []
     for _ in range(args.warmup):
-        _, _, _, inf = J.svd(A, out=(U, S, V), return_info=True, **kw)
+        solve(A)
     torch.cuda.synchronize()
 
     # FP64 peak of this GPU, measured now (warm clocks), for the roofline
@@ -211,7 +294,7 @@ def run_gpu(args) -> None:
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        _, _, _, inf = J.svd(A, out=(U, S, V), return_info=True, **kw)
+        _, _, _, inf = solve(A)
         infos.append(inf)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -244,7 +327,7 @@ def run_gpu(args) -> None:
         f0.record(stream)
         for _ in range(args.e2e_steps):
             A_dev.copy_(A_pin, non_blocking=True)
-            J.svd(A_dev.t(), out=(U, S, V), **kw)
+            solve(A_dev.t())
             U_h.copy_(U.t(), non_blocking=True)
             S_h.copy_(S, non_blocking=True)
             V_h.copy_(V.t(), non_blocking=True)
@@ -283,10 +366,45 @@ def run_gpu(args) -> None:
                for c in ("gram", "jacobi", "update")}
 
     cpu = None
+    mixed_report = None
+    if kind == "mixed" and not args.no_compare:
+        # plain FP64 run of the same matrix, outside the timed region
+        kw64 = dict(kw)
+        kw64.pop("precision")
+        U64 = torch.empty_like(U)
+        S64 = torch.empty_like(S)
+        V64 = torch.empty_like(V)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        _, _, _, inf64 = J.svd(A, out=(U64, S64, V64), return_info=True, **kw64)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        s64 = S64.cpu().numpy()
+        smx = S.cpu().numpy()
+        rel = np.abs(smx - s64) / s64
+        s_true = np.sort(10.0 ** (-12.0 * np.random.default_rng(args.seed).uniform(0.0, 1.0, size=n)))[::-1]
+        mixed_report = {
+            "plain_fp64_s": g0.elapsed_time(g1) / 1e3, "mixed_s": ms_step / 1e3,
+            "speedup": (g0.elapsed_time(g1) / 1e3) / (ms_step / 1e3),
+            "plain_sweeps": inf64["sweeps"], "mixed_sweeps_fp32": infos[-1]["sweeps_low"],
+            "mixed_sweeps_fp64": infos[-1]["sweeps"],
+            "normwise_vs_plain": float(np.max(np.abs(smx - s64)) / s64[0]),
+            "max_rel_vs_plain": float(rel.max()),
+            "rel_vs_plain_by_decade": {f"1e{-d}..1e{-d-1}": float(rel[(s64 <= 10.0 ** -d) & (s64 > 10.0 ** (-d - 1))].max())
+                                       for d in range(0, 12) if np.any((s64 <= 10.0 ** -d) & (s64 > 10.0 ** (-d - 1)))},
+            "normwise_mixed_vs_planted": float(np.max(np.abs(smx - s_true)) / s_true[0]),
+            "normwise_plain_vs_planted": float(np.max(np.abs(s64 - s_true)) / s_true[0]),
+            "orth_V_mixed": float((V.t() @ V - torch.eye(n, device=dev, dtype=torch.float64)).abs().max()),
+        }
+
+    cpu = None
     if world == 1 and not args.no_cpu:
         sweeps = statistics.mean(i["sweeps"] for i in infos)
+        if mixed_report:
+            sweeps = mixed_report["plain_sweeps"]
         est, sample = cpu_sample(A_host, args.b if args.b else infos[-1]["b"], args.strategy,
-                                 args.cpu_pairs, sweeps)
+                                 args.cpu_pairs, sweeps, n // 2 if kind == "hsvd" else None)
         cpu = {"value": est, "unit": "s/matrix", "cores": 1, "kind": "oracle", "sample": sample}
 
     last = infos[-1]
@@ -304,6 +422,8 @@ def run_gpu(args) -> None:
         "gpu_launches": int(sum(v[1] for v in prof.values())),
         "clocks": clk,
     }
+    if mixed_report:
+        line["mixed_vs_plain"] = mixed_report
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -315,7 +435,8 @@ def main():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="graded8192", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="graded8192", choices=sorted(WORKLOADS) + ["batched4096"])
+    p.add_argument("--batch", type=int, default=4096)
     p.add_argument("--b", type=int, default=32)
     p.add_argument("--strategy", default="rR")
     p.add_argument("--max-sweeps", type=int, default=30)
@@ -323,6 +444,7 @@ def main():
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-compare", action="store_true")
     p.add_argument("--cpu-pairs", type=int, default=32)
     p.add_argument("--peak-seconds", type=float, default=2.0)
     p.add_argument("--cpu-sweeps", type=float, default=12.0,
@@ -330,6 +452,8 @@ def main():
     args = p.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched4096":
+        run_batched(args)
     else:
         run_gpu(args)
 

@@ -113,6 +113,40 @@ int jsvd_dhsvj(jsvd_ctx_t ctx, int m, int n, int n_plus, const double *G, int ld
                double *S, double *U, int ldu, double *V, int ldv,
                const jsvd_opts *opts, jsvd_info *info);
 
+/* Batched SVD of `batch` independent matrices of uneven sizes, in one CUDA
+ * graph launch (not in the paper; the per-matrix method is the one above).
+ *   m, n   : host arrays (batch): m[i] >= n[i] >= 1, n[i] <= 1024 after
+ *            bordering to a multiple of 2b
+ *   b      : host array of block widths (8, 16 or 32) or NULL: opts->b, else
+ *            8 for n <= 256 and 16 above
+ *   A      : device, packed: A_i (m_i x n_i, column-major, ld m_i) starts at
+ *            A + a_off[i]; read only
+ *   S, U, V: device, packed likewise: S_i (n_i) at S + s_off[i], U_i (m_i x n_i,
+ *            ld m_i) at U + u_off[i], V_i (n_i x n_i, ld n_i) at V + v_off[i];
+ *            V may be NULL (then v_off may be NULL)
+ *   a_off, s_off, u_off, v_off: host arrays (batch) of element offsets
+ *   infos  : host array (batch) or NULL; filled after the run completes.
+ * Every matrix runs the block-oriented method to its own convergence (or
+ * opts->max_sweeps); opts->precision must be JSVD_PREC_FP64.  Returns
+ * JSVD_NOT_CONVERGED if any matrix hit the sweep limit.                     */
+int jsvd_dgesvj_batched(jsvd_ctx_t ctx, int batch, const int *m, const int *n, const int *b,
+                        const double *A, const long long *a_off, double *S, const long long *s_off,
+                        double *U, const long long *u_off, double *V, const long long *v_off,
+                        const jsvd_opts *opts, jsvd_info *infos);
+
+/* Reverse-mode derivative (adjoint) of A_i = U_i diag(S_i) V_i^T for a batch
+ * packed as in jsvd_dgesvj_batched (not in the paper; the published SVD
+ * adjoint with F_ij = 1/(s_j^2 - s_i^2) evaluated in the split form
+ * (a+c)/(2(s_j-s_i)) + (a-c)/(2(s_j+s_i))).  dU, dS, dV are packed like U, S,
+ * V and may each be NULL (zero cotangent); dA_i (m_i x n_i, ld m_i) is written
+ * at dA + a_off[i].  Needs distinct, positive singular values; U_i with
+ * orthonormal columns and V_i orthogonal.  All pointers device except the
+ * host arrays m, n and the offsets.                                          */
+int jsvd_dgesvj_backward(jsvd_ctx_t ctx, int batch, const int *m, const int *n, const double *U,
+                         const long long *u_off, const double *S, const long long *s_off, const double *V,
+                         const long long *v_off, const double *dU, const double *dS, const double *dV,
+                         double *dA, const long long *a_off);
+
 /* The block p-strategy table of order nblocks (even, >= 2) for `strategy`:
  * out_pairs (host, 2*(nblocks-1)*(nblocks/2) ints) receives, p-step by p-step,
  * the 0-based pairs (p, q), p < q.  The R/C families need nblocks = 2^k * o

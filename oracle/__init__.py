@@ -62,8 +62,8 @@ def _load():
             lib.jo_rot.restype = I
             lib.jo_rot_batch.argtypes = [I, P, P, P, P, I, P, P, P]
             lib.jo_hestenes.argtypes = [I, I, I, P, I, P, I, P, I, I, I, D, P, P]
-            lib.jo_block_pstep.argtypes = [I, I, I, I, P, I, P, I, P, I, P, I, P]
-            lib.jo_block_svd.argtypes = [I, I, I, I, P, I, P, I, P, I, I, P, I, I, P, P]
+            lib.jo_block_pstep.argtypes = [I, I, I, I, P, I, P, I, P, I, P, I, I, I, P]
+            lib.jo_block_svd.argtypes = [I, I, I, I, P, I, P, I, P, I, I, P, I, I, I, I, P, P]
             lib.jo_colnorms.argtypes = [I, I, P, I, P]
             lib.jo_svd_adjoint.argtypes = [I, I, P, P, P, P, P, P, P]
             _lib = lib
@@ -170,7 +170,7 @@ def hsvd(G, nplus: int, strategy: str = "rR", max_sweeps: int = 100):
 
 
 def block_pstep(G, V, b: int, step_pairs, inner_table, nplus: int | None = None,
-                inner_sweeps: int = 1):
+                inner_sweeps: int = 1, border: tuple[int, int] = (0, 0)):
     """One p-step of the block-oriented method on copies of G and V."""
     G = _fortran(G).copy(order="F")
     V = _fortran(V).copy(order="F")
@@ -180,18 +180,35 @@ def block_pstep(G, V, b: int, step_pairs, inner_table, nplus: int | None = None,
     it = np.ascontiguousarray(np.asarray(inner_table, dtype=np.int32))
     stats = np.zeros(4, dtype=np.int64)
     _load().jo_block_pstep(m, n, nplus, b, _ptr(G), m, _ptr(V), n, _ptr(sp), sp.shape[0],
-                           _ptr(it), inner_sweeps, _ptr(stats))
+                           _ptr(it), inner_sweeps, border[0], border[1], _ptr(stats))
     return G, V, dict(rotations=int(stats[0]), proper=int(stats[1]),
                       updated=int(stats[2]), breakdowns=int(stats[3]))
 
 
+def bordered(A, b: int, nplus: int | None = None):
+    """Identity bordering [[G, 0], [0, I_k]] up to the next multiple of 2b
+    columns (for the HSVD the border columns are inserted at the J boundary):
+    returns (the bordered matrix, (first, last+1) border column, n_plus of it)."""
+    A = _fortran(A)
+    m, n = A.shape
+    nplus = n if nplus is None else nplus
+    n_pad = max(2 * b, -(-n // (2 * b)) * 2 * b)
+    k = n_pad - n
+    B = np.zeros((m + k, n_pad))
+    B[:m, :nplus] = A[:, :nplus]
+    B[:m, nplus + k:] = A[:, nplus:]
+    B[m:, nplus:nplus + k] = np.eye(k)
+    return np.asfortranarray(B), (nplus, nplus + k), nplus + k
+
+
 def block_svd(A, b: int, strategy: str = "rR", inner_strategy: str | None = None,
-              nplus: int | None = None, inner_sweeps: int = 1, max_sweeps: int = 30):
+              nplus: int | None = None, inner_sweeps: int = 1, max_sweeps: int = 30,
+              border: tuple[int, int] = (0, 0)):
     """The block-oriented method (Sec. 2, 4) on CPU: raw G, V and statistics."""
     G = _fortran(A).copy(order="F")
     m, n = G.shape
     if n % (2 * b):
-        raise ValueError("n must be a multiple of 2b")
+        raise ValueError("n must be a multiple of 2b (see bordered())")
     nb = n // b
     nplus = n if nplus is None else nplus
     V = np.asfortranarray(np.eye(n))
@@ -200,7 +217,8 @@ def block_svd(A, b: int, strategy: str = "rR", inner_strategy: str | None = None
     stats = np.zeros(6, dtype=np.int64)
     per = np.zeros(max_sweeps, dtype=np.int64)
     _load().jo_block_svd(m, n, nplus, b, _ptr(G), m, _ptr(V), n, _ptr(tab), tab.shape[0],
-                         tab.shape[1], _ptr(it), inner_sweeps, max_sweeps, _ptr(stats), _ptr(per))
+                         tab.shape[1], _ptr(it), inner_sweeps, max_sweeps, border[0], border[1],
+                         _ptr(stats), _ptr(per))
     return dict(G=G, V=V, sweeps=int(stats[0]), converged=bool(stats[1]), rotations=int(stats[2]),
                 proper=int(stats[3]), updated=int(stats[4]), breakdowns=int(stats[5]),
                 proper_per_sweep=per[: stats[0]].copy())

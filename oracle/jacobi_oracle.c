@@ -37,6 +37,12 @@
  *       no swap happened).
  *   R5  a non-positive (or NaN) Cholesky pivot is a breakdown: the pivot
  *       column of L is set to zero and the event is counted.
+ *   R7  identity bordering [[G, 0], [0, I]] (used when n is not a multiple of
+ *       2b): the border columns are exactly orthogonal to every column and
+ *       are neither rotated nor swapped by the P2 sort, so they keep their
+ *       positions (otherwise a sort swap with a unit-norm border column can
+ *       carry a matrix column past its partner for a whole sweep and end the
+ *       iteration with the pair unrotated).
  *   R6  sgn(x) is copysign(1, x), so sgn(+0) = +1 and sgn(-0) = -1.
  */
 #include <math.h>
@@ -129,8 +135,10 @@ static void swap_cols(int len, double *x, double *y)
  * Returns bit 0: rotation applied (rho), bit 1: proper (cs != 1),
  * bit 2: columns swapped by P2.                                            */
 static int jo_pair(int m, double *gp, double *gq, int nv, double *vp, double *vq,
-                   int k, int l, int nplus, double c_eps)
+                   int k, int l, int nplus, double c_eps, int bord_lo, int bord_hi)
 {
+    if ((k >= bord_lo && k < bord_hi) || (l >= bord_lo && l < bord_hi))
+        return 0;                                       /* R7 */
     double hpp = dot(m, gp, gp);
     double hqq = dot(m, gq, gq);
     double hpq = dot(m, gp, gq);
@@ -192,7 +200,7 @@ void jo_hestenes(int m, int n, int nplus, double *G, int ldg, double *V, int ldv
                                 V ? n : 0,
                                 V ? V + (size_t)p * ldv : NULL,
                                 V ? V + (size_t)q * ldv : NULL,
-                                p, q, nplus, c_eps);
+                                p, q, nplus, c_eps, 0, 0);
                 rot += f & 1;
                 tot_proper += (f >> 1) & 1;
                 tot_swap += (f >> 2) & 1;
@@ -251,10 +259,12 @@ static int cholesky_lower(int bb, double *H, double *L)
  *   the rotation type from the global column indices, the P2 sort  Sec. 4.3
  *   [G_P G_Q] := [G_P G_Q] V', [V_P V_Q] := [V_P V_Q] V'  (2.9), R4
  * stats (accumulated): [0] rotations, [1] proper rotations, [2] block pairs
- * updated, [3] Cholesky breakdowns.                                        */
+ * updated, [3] Cholesky breakdowns.  Columns in [bord_lo, bord_hi) are an
+ * identity border (R7; pass bord_lo = bord_hi for none).                    */
 void jo_block_pstep(int m, int n, int nplus, int b, double *G, int ldg,
                     double *V, int ldv, const int *step_pairs, int npairs,
-                    const int *inner_table, int inner_sweeps, long long *stats)
+                    const int *inner_table, int inner_sweeps, int bord_lo, int bord_hi,
+                    long long *stats)
 {
     const int bb = 2 * b;
     const double c_eps = JO_EPS * sqrt((double)bb);
@@ -296,7 +306,7 @@ void jo_block_pstep(int m, int n, int nplus, int b, double *G, int ldg,
                     int q = inner_table[2 * (s * b + y) + 1];
                     int f = jo_pair(bb, R + (size_t)p * bb, R + (size_t)q * bb,
                                     bb, W + (size_t)p * bb, W + (size_t)q * bb,
-                                    gidx[p], gidx[q], nplus, c_eps);
+                                    gidx[p], gidx[q], nplus, c_eps, bord_lo, bord_hi);
                     a_r += f & 1;
                     stats[1] += (f >> 1) & 1;
                     if (f) changed = 1;
@@ -338,7 +348,7 @@ void jo_block_pstep(int m, int n, int nplus, int b, double *G, int ldg,
 void jo_block_svd(int m, int n, int nplus, int b, double *G, int ldg,
                   double *V, int ldv, const int *table, int nsteps, int npairs,
                   const int *inner_table, int inner_sweeps, int max_sweeps,
-                  long long *stats, long long *proper_per_sweep)
+                  int bord_lo, int bord_hi, long long *stats, long long *proper_per_sweep)
 {
     long long acc[4] = {0, 0, 0, 0};
     int sweep, converged = 0;
@@ -347,7 +357,7 @@ void jo_block_svd(int m, int n, int nplus, int b, double *G, int ldg,
         for (int s = 0; s < nsteps; ++s)
             jo_block_pstep(m, n, nplus, b, G, ldg, V, ldv,
                            table + (size_t)2 * s * npairs, npairs,
-                           inner_table, inner_sweeps, acc);
+                           inner_table, inner_sweeps, bord_lo, bord_hi, acc);
         long long B = acc[1] - before;
         if (proper_per_sweep) proper_per_sweep[sweep] = B;
         if (B == 0) { converged = 1; ++sweep; break; }

@@ -15,6 +15,7 @@
 #include "jsvd.h"
 #include "jsvd_internal.h"
 #include "driver.h"
+#include "gemm_fp64.cuh"
 #include "rotation.cuh"
 #include "sweep_fp64.cuh"
 
@@ -106,6 +107,37 @@ __global__ void k_finalize(const double *__restrict__ G, int ldg, const double *
     }
 }
 
+__global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, size_t count) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        y[e] = (float)x[e];
+}
+
+__global__ void k_eye_f32(float *__restrict__ V, int ldv, int v_rows, int n_pad) {
+    const size_t total = (size_t)v_rows * n_pad;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % v_rows), c = (int)(e / v_rows);
+        V[(size_t)c * ldv + r] = (r == c) ? 1.f : 0.f;
+    }
+}
+
+// E := S - I (in place), n x n, ld n.
+__global__ void k_sub_eye(double *__restrict__ S, int n) {
+    const size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+        if (e % n == e / n) S[e] = S[e] - 1.0;
+}
+
+// M := I - E/2 + (3/8) E^2 (into E2), the first terms of (I + E)^{-1/2}.
+__global__ void k_polar_combine(const double *__restrict__ E, double *__restrict__ E2, int n) {
+    const size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        double v = __fma_rn(0.375, E2[e], -0.5 * E[e]);
+        if (e % n == e / n) v += 1.0;
+        E2[e] = v;
+    }
+}
+
 __global__ void k_rot_params(int count, const double *hpp, const double *hqq, const double *hpq,
                              const int *hyp, double *cs, double *tn, int *proper) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,7 +224,10 @@ int jsvd_ctx::inner_table(int strategy, int BB, const unsigned char **dev) {
 }
 
 jsvd_ctx::~jsvd_ctx() {
-    for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm})
+    for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &g32, &v32,
+                      &tmp_a, &tmp_b, &tmp_g, &b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag,
+                      &b_tab, &b_cnt, &b_stat, &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &adj_w,
+                      &adj_meta, &adj_desc})
         if (b->ptr) cudaFree(b->ptr);
     for (auto &kv : tables)
         if (kv.second.ptr) cudaFree(kv.second.ptr);
@@ -207,6 +242,40 @@ int jsvd_ctx::ensure_events(size_t count) {
         events.push_back(e);
     }
     return 0;
+}
+
+int jsvd_ctx::sync(const char *where) {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        set_error(where, e);
+        return JSVD_ERR_CUDA;
+    }
+    return check(where);
+}
+
+// Mixed precision, stage 2.  V32 (FP32, n x n inside an ld-v32 buffer) is
+// orthogonal to about the FP32 unit roundoff; its polar factor is
+//   Q = V32 (V32^T V32)^{-1/2} = V32 (I - E/2 + 3E^2/8 - ...),  E = V32^T V32 - I,
+// and with ||E|| ~ 1e-6 the truncation error ~||E||^3 is below the FP64 unit
+// roundoff.  Then G := G Q and V := Q, all in FP64.
+int jsvd_ctx::polar_and_apply(double *G, int ldg, int n, const float *V32, int ldv32, double *V, int ldv) {
+    int rc;
+    const size_t nn = (size_t)n * n;
+    if ((rc = ensure(tmp_a, sizeof(double) * nn))) return rc;
+    if ((rc = ensure(tmp_b, sizeof(double) * nn))) return rc;
+    if ((rc = ensure(tmp_g, sizeof(double) * (size_t)ldg * n))) return rc;
+    double *E = (double *)tmp_a.ptr, *E2 = (double *)tmp_b.ptr, *G2 = (double *)tmp_g.ptr;
+    gemm(true, false, Elt::F32, Elt::F32, n, n, n, 1.0, V32, ldv32, V32, ldv32, 0.0, E, n, stream);
+    k_sub_eye<<<1024, 256, 0, stream>>>(E, n);
+    gemm(false, false, Elt::F64, Elt::F64, n, n, n, 1.0, E, n, E, n, 0.0, E2, n, stream);
+    k_polar_combine<<<1024, 256, 0, stream>>>(E, E2, n);
+    gemm(false, false, Elt::F32, Elt::F64, n, n, n, 1.0, V32, ldv32, E2, n, 0.0, V, ldv, stream);
+    gemm(false, false, Elt::F64, Elt::F64, ldg, n, n, 1.0, G, ldg, V, ldv, 0.0, G2, ldg, stream);
+    cudaMemcpyAsync(G, G2, sizeof(double) * (size_t)ldg * n, cudaMemcpyDeviceToDevice, stream);
+    prof_launches[3] += 6;
+    const double nd = (double)n;
+    prof_flops[3] += 2.0 * nd * nd * nd * 3.0 + 2.0 * (double)ldg * nd * nd;
+    return check("polar");
 }
 
 // ---------------------------------------------------------------------------
@@ -235,8 +304,8 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
     if (o.inner_sweeps <= 0) o.inner_sweeps = 1;
     if (o.inner_strategy < 0) o.inner_strategy = o.strategy;
     if (o.strategy < 0 || o.strategy > 4 || o.inner_strategy > 4) return JSVD_ERR_UNSUPPORTED;
-    if (o.precision != JSVD_PREC_FP64) {
-        last_error = "precision mode not available in this entry point";
+    if (o.precision != JSVD_PREC_FP64 && o.precision != JSVD_PREC_MIXED) {
+        last_error = "unknown precision mode";
         return JSVD_ERR_UNSUPPORTED;
     }
     const int b = choose_b(o, n);
@@ -283,75 +352,107 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
 
     double *G = (double *)g.ptr, *V = (double *)v.ptr;
     unsigned long long *cnt = (unsigned long long *)counters.ptr;
+    const bool mixed = o.precision == JSVD_PREC_MIXED;
+    const bool want_v = Vout != nullptr || mixed;
 
     cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
     k_init_g<<<1024, 256, 0, stream>>>(A, lda, m, n, ins, k, G, g_rows, g_rows, n_pad, cnt + kCntErr);
-    k_eye<<<1024, 256, 0, stream>>>(V, v_rows, v_rows, n_pad);
-    prof_launches[3] += 2;
+    prof_launches[3] += 1;
+    if (want_v) {
+        k_eye<<<1024, 256, 0, stream>>>(V, v_rows, v_rows, n_pad);
+        prof_launches[3] += 1;
+    }
     if (profiling && (rc = ensure_events(4 * (size_t)(nb - 1)))) return rc;
-    const double bbd = (double)BB;
-    const double fl_gram = (double)npairs * m * bbd * (bbd + 1.0);
-    const double fl_jac = (double)npairs * (9.0 * bbd * bbd * (bbd - 1.0) + bbd * bbd * bbd / 3.0);
-    const double fl_upd_pair = 2.0 * ((double)m + (Vout ? (double)n : 0.0)) * bbd * bbd;
     if ((rc = check("init"))) return rc;
     cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize, cudaMemcpyDeviceToHost, stream);
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return check("init sync") ? JSVD_ERR_CUDA : JSVD_ERR_CUDA;
+    if ((rc = sync("init"))) return rc;
     if (host_counters[kCntErr]) {
         last_error = "input holds Inf or NaN";
         return JSVD_ERR_NONFINITE;
     }
 
     PStepArgs a{};
-    a.G = G; a.ldg = g_rows; a.g_rows = g_rows;
-    a.V = V; a.ldv = v_rows; a.v_rows = v_rows;
+    a.ldg = g_rows; a.g_rows = g_rows;
+    a.ldv = v_rows; a.v_rows = v_rows;
     a.table = dtab; a.npairs = npairs; a.inner = dinner;
     a.b = b; a.nplus = nplus_w; a.inner_sweeps = o.inner_sweeps;
+    a.bord_lo = ins; a.bord_hi = ins + k;
     a.part = (double *)part.ptr; a.g_chunks = g_chunks;
     a.vprime = (double *)vprime.ptr; a.vflag = (int *)vflag.ptr;
     a.counters = cnt;
 
+    const double bbd = (double)BB;
+    const double fl_gram = (double)npairs * m * bbd * (bbd + 1.0);
+    const double fl_jac = (double)npairs * (9.0 * bbd * bbd * (bbd - 1.0) + bbd * bbd * bbd / 3.0);
+    const double fl_upd_pair = 2.0 * ((double)m + (want_v ? (double)n : 0.0)) * bbd * bbd;
+
     jsvd_info inf{};
     inf.b = b;
-    int converged = 0, sweeps = 0;
-    for (sweeps = 0; sweeps < o.max_sweeps;) {
-        cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
-        for (int s = 0; s < nb - 1; ++s) {
-            a.step = s;
-            launch_pstep_fp64(BB, a, stream, profiling ? &events[4 * (size_t)s] : nullptr);
+    // Block sweeps until a sweep has no proper rotation (Sec. 4.5) or the limit.
+    auto sweep_loop = [&](int limit, int *done, int *conv) -> int {
+        *done = 0;
+        *conv = 0;
+        while (*done < limit) {
+            cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
+            for (int s = 0; s < nb - 1; ++s) {
+                a.step = s;
+                launch_pstep_fp64(BB, a, stream, profiling ? &events[4 * (size_t)s] : nullptr);
+            }
+            prof_launches[0] += nb - 1;
+            prof_launches[1] += nb - 1;
+            prof_launches[2] += nb - 1;
+            if (int r = check("p-step")) return r;
+            cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize,
+                            cudaMemcpyDeviceToHost, stream);
+            if (int r = sync("sweep")) return r;
+            ++*done;
+            prof_flops[0] += fl_gram * (nb - 1);
+            prof_flops[1] += fl_jac * (nb - 1);
+            prof_flops[2] += fl_upd_pair * (double)host_counters[kCntUpdated];
+            if (profiling) {
+                for (int s = 0; s < nb - 1; ++s)
+                    for (int c = 0; c < 3; ++c) {
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, events[4 * (size_t)s + c], events[4 * (size_t)s + c + 1]);
+                        prof_ms[c] += ms;
+                    }
+            }
+            inf.rotations += (long long)host_counters[kCntRot];
+            inf.proper_rotations += (long long)host_counters[kCntProper];
+            inf.pairs_updated += (long long)host_counters[kCntUpdated];
+            inf.breakdowns += (long long)host_counters[kCntBreak];
+            double off;
+            unsigned long long bits = host_counters[kCntOff];
+            memcpy(&off, &bits, sizeof off);
+            inf.off_norm = off;
+            if (verbose)
+                fprintf(stderr, "[jsvd] %s sweep %d: rotations %llu proper %llu updated %llu off %.3e\n",
+                        a.fp32 ? "fp32" : "fp64", *done, host_counters[kCntRot], host_counters[kCntProper],
+                        host_counters[kCntUpdated], off);
+            if (host_counters[kCntProper] == 0) { *conv = 1; break; }
         }
-        prof_launches[0] += nb - 1;
-        prof_launches[1] += nb - 1;
-        prof_launches[2] += nb - 1;
-        if ((rc = check("p-step"))) return rc;
-        cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize,
-                        cudaMemcpyDeviceToHost, stream);
-        cudaError_t e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) { set_error("sweep", e); return JSVD_ERR_CUDA; }
-        ++sweeps;
-        prof_flops[0] += fl_gram * (nb - 1);
-        prof_flops[1] += fl_jac * (nb - 1);
-        prof_flops[2] += fl_upd_pair * (double)host_counters[kCntUpdated];
-        if (profiling) {
-            for (int s = 0; s < nb - 1; ++s)
-                for (int c = 0; c < 3; ++c) {
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, events[4 * (size_t)s + c], events[4 * (size_t)s + c + 1]);
-                    prof_ms[c] += ms;
-                }
-        }
-        inf.rotations += (long long)host_counters[kCntRot];
-        inf.proper_rotations += (long long)host_counters[kCntProper];
-        inf.pairs_updated += (long long)host_counters[kCntUpdated];
-        inf.breakdowns += (long long)host_counters[kCntBreak];
-        double off;
-        unsigned long long bits = host_counters[kCntOff];
-        memcpy(&off, &bits, sizeof off);
-        inf.off_norm = off;
-        if (verbose)
-            fprintf(stderr, "[jsvd] sweep %d: rotations %llu proper %llu updated %llu off %.3e\n", sweeps,
-                    host_counters[kCntRot], host_counters[kCntProper], host_counters[kCntUpdated], off);
-        if (host_counters[kCntProper] == 0) { converged = 1; break; }
+        return 0;
+    };
+
+    if (mixed) {
+        // Stage 1: FP32 block sweeps on copies G32 = fl32(G), V32 = I, with the
+        // relative test at the FP32 unit roundoff.
+        if ((rc = ensure(g32, sizeof(float) * (size_t)g_rows * n_pad))) return rc;
+        if ((rc = ensure(v32, sizeof(float) * (size_t)v_rows * n_pad))) return rc;
+        float *G32 = (float *)g32.ptr, *V32 = (float *)v32.ptr;
+        k_to_f32<<<1024, 256, 0, stream>>>(G, G32, (size_t)g_rows * n_pad);
+        k_eye_f32<<<1024, 256, 0, stream>>>(V32, v_rows, v_rows, n_pad);
+        prof_launches[3] += 2;
+        a.G = G32; a.V = V32; a.fp32 = 1; a.eps = 0x1p-24;
+        int low_done = 0, low_conv = 0;
+        if ((rc = sweep_loop(o.max_sweeps, &low_done, &low_conv))) return rc;
+        inf.sweeps_low = low_done;
+        // Stage 2: Q = polar factor of V32 in FP64, G := G Q, V := Q.
+        if ((rc = polar_and_apply(G, g_rows, n_pad, V32, v_rows, V, v_rows))) return rc;
     }
+    a.G = G; a.V = want_v ? V : nullptr; a.fp32 = 0; a.eps = kEps;
+    int converged = 0, sweeps = 0;
+    if ((rc = sweep_loop(o.max_sweeps, &sweeps, &converged))) return rc;
     inf.sweeps = sweeps;
     inf.converged = converged;
 
@@ -365,15 +466,15 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
     std::vector<int> hb(n_pad);
     cudaMemcpyAsync(hs.data(), dsig, sizeof(double) * n_pad, cudaMemcpyDeviceToHost, stream);
     cudaMemcpyAsync(hb.data(), dbd, sizeof(int) * n_pad, cudaMemcpyDeviceToHost, stream);
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return check("sigma sync") ? JSVD_ERR_CUDA : JSVD_ERR_CUDA;
+    if ((rc = sync("sigma"))) return rc;
     std::vector<int> pos, neg;
     for (int c = 0; c < n_pad; ++c) {
-        if (hb[c]) continue;
+        if (c >= ins && c < ins + k) continue;   // the border keeps its positions
+        if (hb[c]) {
+            last_error = "a matrix column has support in the border rows";
+            return JSVD_ERR_CUDA;
+        }
         (c < nplus_w ? pos : neg).push_back(c);
-    }
-    if ((int)(pos.size() + neg.size()) != n) {
-        last_error = "border columns could not be separated from the matrix columns";
-        return JSVD_ERR_CUDA;
     }
     if (o.sort) {
         auto desc = [&](int x, int y) { return hs[x] > hs[y]; };
@@ -388,7 +489,7 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
                                          nplus, hyperbolic ? 1 : 0, S, U, ldu, Vout, ldv);
     if ((rc = check("finalize"))) return rc;
     // the host vector hp must outlive the async copy
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return check("final sync") ? JSVD_ERR_CUDA : JSVD_ERR_CUDA;
+    if ((rc = sync("finalize"))) return rc;
     if (info) *info = inf;
     return converged ? JSVD_SUCCESS : JSVD_NOT_CONVERGED;
 }

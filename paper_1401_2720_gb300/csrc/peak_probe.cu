@@ -11,7 +11,8 @@
 
 namespace {
 
-constexpr int kChains = 8;
+constexpr int kChains = 16;   // independent FMA chains per thread
+constexpr int kMma = 8;       // independent mma accumulators per warp
 
 __global__ void probe_dfma(double *out, int iters) {
     double a[kChains];
@@ -32,17 +33,19 @@ __global__ void probe_dfma(double *out, int iters) {
 
 __global__ void probe_dmma(double *out, int iters) {
     const double a = 1e-3 * (threadIdx.x & 7), b = 0.5;
-    double c[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    double c[kMma][2];
+#pragma unroll
+    for (int j = 0; j < kMma; ++j) c[j][0] = c[j][1] = 0.0;
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < kMma; ++j)
             asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
                          : "+d"(c[j][0]), "+d"(c[j][1])
                          : "d"(a), "d"(b));
     }
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) s += c[j][0] + c[j][1];
+    for (int j = 0; j < kMma; ++j) s += c[j][0] + c[j][1];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -54,7 +57,7 @@ extern "C" int jsvd_fp64_peak(jsvd_ctx_t ctx, double seconds, double *dfma_tflop
     cudaSetDevice(ctx->device);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    const int blocks = sms * 4, threads = 256;
+    const int blocks = sms * 8, threads = 256;
     double *buf = nullptr;
     if (cudaMalloc(&buf, sizeof(double) * blocks * threads) != cudaSuccess) return ctx->check("probe alloc");
     cudaEvent_t e0, e1;
@@ -80,7 +83,7 @@ extern "C" int jsvd_fp64_peak(jsvd_ctx_t ctx, double seconds, double *dfma_tflop
         }
         if (rc) break;
         const double fl = kind == 0 ? 2.0 * kChains * 8 * (double)iters * blocks * threads
-                                    : 2.0 * 8 * 8 * 4 * 4 * (double)iters * blocks * (threads / 32);
+                                    : 2.0 * 8 * 8 * 4 * kMma * (double)iters * blocks * (threads / 32);
         const double tf = fl / (ms * 1e-3) / 1e12;
         if (kind == 0 && dfma_tflops) *dfma_tflops = tf;
         if (kind == 1 && dmma_tflops) *dmma_tflops = tf;

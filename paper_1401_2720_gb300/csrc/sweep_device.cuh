@@ -1,0 +1,341 @@
+// Device-side building blocks of one block p-step (Sec. 2, Sec. 4 of the
+// paper), shared by the single-matrix kernels (sweep_fp64.cu) and the batched
+// kernels (batched.cu).  Each function is executed by a whole CTA and handles
+// one unit of work:
+//   gram_unit    the lower triangle of [G_P G_Q]^T [G_P G_Q] over one chunk
+//                of rows (Eq. (2.7), split over rows)
+//   jacobi_unit  sum of the chunk partials, Cholesky (Sec. 4.1), M_s inner
+//                sweeps (Sec. 4.3) accumulated into V', counters
+//   update_unit  one chunk of rows of [A_P A_Q] := [A_P A_Q] V' (Eq. (2.9))
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rotation.cuh"
+
+namespace jsvd {
+
+enum {
+    kCntRot = 0,       // rotations (rho = 1)
+    kCntProper = 1,    // proper rotations (cs != 1)
+    kCntUpdated = 2,   // block pairs with V' != I
+    kCntBreak = 3,     // Cholesky breakdowns
+    kCntOff = 4,       // max normalized off-diagonal |h_ij|/sqrt(h_ii h_jj), double bits
+    kCntErr = 5,       // device-side error flags
+    kCntSize = 8
+};
+
+constexpr int kGramRows = 128;     // rows of [G_P G_Q] per Gram unit
+constexpr int kGramThreads = 256;
+constexpr int kUpdThreads = 256;   // 4x4 output tiles per thread
+
+template <int BB> struct Cfg {
+    static constexpr int kPairsInner = BB / 2;
+    static constexpr int kLanesPerPair = 8;
+    static constexpr int kJacThreads = kPairsInner * kLanesPerPair;   // 4*BB
+    static constexpr int kRowsPerLane = BB / kLanesPerPair;
+    static constexpr int kLd = BB + 1;                                // smem ld for R, V'
+    static constexpr int kPacked = BB * (BB + 1) / 2;
+    static constexpr int kUpdRows = 4096 / BB;                        // rows per update unit
+    static constexpr int kGramLd = BB + 2;                            // smem row stride
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+template <int BB, typename T>
+constexpr size_t gram_smem_bytes() { return sizeof(T) * kGramRows * Cfg<BB>::kGramLd; }
+template <int BB>
+constexpr size_t jacobi_smem_bytes() { return sizeof(double) * 2 * BB * Cfg<BB>::kLd + (BB - 1) * BB + 16; }
+template <int BB, typename T>
+constexpr size_t update_smem_bytes() { return sizeof(T) * (BB * Cfg<BB>::kUpdRows + BB * (BB + 2)); }
+
+__device__ __forceinline__ int block_col(int P, int Q, int b, int j) {
+    return j < b ? P * b + j : Q * b + (j - b);
+}
+
+// Index of (i, j), i >= j, in the column-major packed lower triangle of order BB.
+template <int BB>
+__device__ __forceinline__ int packed_lower(int i, int j) {
+    return j * BB - (j * (j - 1)) / 2 + (i - j);
+}
+
+// ---------------------------------------------------------------------------
+// Gram partial of rows [r0, r0 + valid) (valid <= kGramRows).  The chunk is
+// staged row-major in shared memory (row stride BB+2) so that every thread
+// reads 2x2 operand blocks with vector loads; thread t owns the 2x2 blocks
+// (I, J), I >= J, t, t+256, ... of the lower triangle and sums over the rows
+// in increasing order.  The result (double) goes to out[packed index].
+template <int BB, typename T>
+__device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int r0, int valid, int P,
+                                          int Q, int b, double *__restrict__ out, T *X) {
+    using C = Cfg<BB>;
+    using T2 = typename Vec2<T>::type;
+    for (int e = threadIdx.x; e < kGramRows * BB; e += kGramThreads) {
+        const int r = e % kGramRows, j = e / kGramRows;
+        if (r < valid) X[r * C::kGramLd + j] = G[(size_t)block_col(P, Q, b, j) * ldg + r0 + r];
+    }
+    __syncthreads();
+    constexpr int NB = BB / 2;
+    constexpr int NBLK = NB * (NB + 1) / 2;
+    for (int blk = threadIdx.x; blk < NBLK; blk += kGramThreads) {
+        int I = (int)((sqrtf(8.0f * blk + 1.0f) - 1.0f) * 0.5f);
+        while ((I + 1) * (I + 2) / 2 <= blk) ++I;
+        while (I * (I + 1) / 2 > blk) --I;
+        const int J = blk - I * (I + 1) / 2;
+        T h00 = 0, h10 = 0, h01 = 0, h11 = 0;
+        const T *xi = X + 2 * I, *xj = X + 2 * J;
+#pragma unroll 4
+        for (int r = 0; r < valid; ++r) {
+            const T2 u = *reinterpret_cast<const T2 *>(xi + r * C::kGramLd);
+            const T2 v = *reinterpret_cast<const T2 *>(xj + r * C::kGramLd);
+            h00 = fma(u.x, v.x, h00);
+            h10 = fma(u.y, v.x, h10);
+            h01 = fma(u.x, v.y, h01);
+            h11 = fma(u.y, v.y, h11);
+        }
+        const int i0 = 2 * I, j0 = 2 * J;
+        out[packed_lower<BB>(i0, j0)] = (double)h00;
+        out[packed_lower<BB>(i0 + 1, j0)] = (double)h10;
+        out[packed_lower<BB>(i0 + 1, j0 + 1)] = (double)h11;
+        if (I != J) out[packed_lower<BB>(i0, j0 + 1)] = (double)h01;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-pair factorization and inner sweeps; executed by Cfg<BB>::kJacThreads
+// threads.  smem: A and B, each BB x BB column-major with ld BB+1, then the
+// inner table ((BB-1) x BB/2 pairs of bytes).
+//   A: H (lower) -> L by Cholesky -> V' (= I, then rotated)
+//   B: R = L^T (upper), rotated in the inner sweeps
+// Inner p-step: pair y of the inner table is handled by the 8-lane group y;
+// lane g of the group owns rows g, g+8, ... of both columns in R and V'.
+// Writes V' (column-major, BB x BB) to vp and "V' != I" to *vflag; adds the
+// rotation counts to counters[].  Global columns in [bord_lo, bord_hi) are the
+// identity border: they are exactly orthogonal to everything, and they are
+// neither rotated nor swapped, so they keep their positions.
+template <int BB>
+__device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int chunks,
+                                            const unsigned char *__restrict__ inner, int P, int Q, int b,
+                                            int nplus, int bord_lo, int bord_hi, int inner_sweeps, double eps,
+                                            double *__restrict__ vp,
+                                            int *__restrict__ vflag, unsigned long long *__restrict__ counters,
+                                            double *smem) {
+    using C = Cfg<BB>;
+    double *A = smem;
+    double *B = smem + BB * C::kLd;
+    unsigned char *tab = reinterpret_cast<unsigned char *>(smem + 2 * BB * C::kLd);
+    __shared__ double s_piv;
+    __shared__ int s_brk;
+    __shared__ unsigned long long s_off;
+    __shared__ int s_cnt[2];
+
+    const int tid = threadIdx.x;
+    for (int e = tid; e < (BB - 1) * BB; e += C::kJacThreads) tab[e] = inner[e];
+    if (tid == 0) { s_off = 0ull; s_brk = 0; s_cnt[0] = 0; s_cnt[1] = 0; }
+
+    // (1) H = sum of the row-chunk partials, in chunk order
+    for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+        const int i = e % BB, j = e / BB;
+        if (i < j) continue;
+        const int k = packed_lower<BB>(i, j);
+        double s = 0.0;
+        for (int c = 0; c < chunks; ++c) s = __dadd_rn(s, part[(size_t)c * C::kPacked + k]);
+        A[i + j * C::kLd] = s;
+    }
+    __syncthreads();
+
+    // (2) normalized off-diagonal maximum of H (convergence report)
+    {
+        double mx = 0.0;
+        for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+            const int i = e % BB, j = e / BB;
+            if (i <= j) continue;
+            const double d = A[i + i * C::kLd] * A[j + j * C::kLd];
+            if (d > 0.0) mx = fmax(mx, fabs(A[i + j * C::kLd]) / sqrt(d));
+        }
+        atomicMax(&s_off, (unsigned long long)__double_as_longlong(mx));
+    }
+
+    // (3) Cholesky H = L L^T without pivoting (Sec. 4.1), right-looking:
+    // entry (i, j) receives -L(i,k) L(j,k) for k = 0, 1, ... in order, then the
+    // division by the pivot.  A non-positive pivot zeroes its column.
+    for (int k = 0; k < BB; ++k) {
+        if (tid == 0) {
+            const double d = A[k + k * C::kLd];
+            if (d > 0.0) {
+                s_piv = __dsqrt_rn(d);
+            } else {
+                s_piv = 0.0;
+                s_brk += 1;
+            }
+        }
+        __syncthreads();
+        const double piv = s_piv;
+        for (int i = k + tid; i < BB; i += C::kJacThreads)
+            A[i + k * C::kLd] = (piv > 0.0) ? (i == k ? piv : __ddiv_rn(A[i + k * C::kLd], piv)) : 0.0;
+        __syncthreads();
+        const int rem = BB - 1 - k;
+        for (int e = tid; e < rem * rem; e += C::kJacThreads) {
+            const int i = k + 1 + e % rem, j = k + 1 + e / rem;
+            if (i >= j)
+                A[i + j * C::kLd] = __fma_rn(-A[i + k * C::kLd], A[j + k * C::kLd], A[i + j * C::kLd]);
+        }
+        __syncthreads();
+    }
+
+    // (4) R = L^T into B; V' = I into A
+    for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+        const int i = e % BB, j = e / BB;
+        B[i + j * C::kLd] = (i <= j) ? A[j + i * C::kLd] : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+        const int i = e % BB, j = e / BB;
+        A[i + j * C::kLd] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+
+    // (5) inner sweeps of the pointwise one-sided method on R (Sec. 4.3)
+    const int y = tid / C::kLanesPerPair;
+    const int g = tid % C::kLanesPerPair;
+    const double c_eps = eps * sqrt((double)BB);   // c(eps) = eps sqrt(nhat), nhat = BB
+    int my_rot = 0, my_proper = 0, changed = 0;
+    for (int sw = 0; sw < inner_sweeps; ++sw) {
+        int sweep_rot = 0;
+        for (int st = 0; st < BB - 1; ++st) {
+            const int p = tab[2 * (st * (BB / 2) + y)];
+            const int q = tab[2 * (st * (BB / 2) + y) + 1];
+            double *rp = B + p * C::kLd, *rq = B + q * C::kLd;
+            double *wp = A + p * C::kLd, *wq = A + q * C::kLd;
+            double hpp = 0.0, hqq = 0.0, hpq = 0.0;
+#pragma unroll
+            for (int k = 0; k < C::kRowsPerLane; ++k) {
+                const int r = g + k * C::kLanesPerPair;
+                const double x = rp[r], z = rq[r];
+                hpp = __fma_rn(x, x, hpp);
+                hqq = __fma_rn(z, z, hqq);
+                hpq = __fma_rn(x, z, hpq);
+            }
+#pragma unroll
+            for (int off = C::kLanesPerPair / 2; off > 0; off >>= 1) {
+                hpp = __dadd_rn(hpp, __shfl_xor_sync(0xffffffffu, hpp, off));
+                hqq = __dadd_rn(hqq, __shfl_xor_sync(0xffffffffu, hqq, off));
+                hpq = __dadd_rn(hpq, __shfl_xor_sync(0xffffffffu, hpq, off));
+            }
+            const int gp = block_col(P, Q, b, p), gq = block_col(P, Q, b, q);
+            const double t = (gp < nplus && gq >= nplus) ? -1.0 : 1.0;
+            const bool border = (gp >= bord_lo && gp < bord_hi) || (gq >= bord_lo && gq < bord_hi);
+            const bool rho = !border && needs_rotation(hpp, hqq, hpq, c_eps);
+            Rot rot{1.0, 0.0};
+            if (rho) rot = rot_params(hpp, hqq, hpq, t);
+            bool swap = false;
+            if (t > 0.0 && !border) {
+                const double npp = rho ? __fma_rn(-rot.tn, hpq, hpp) : hpp;
+                const double nqq = rho ? __fma_rn(rot.tn, hpq, hqq) : hqq;
+                swap = (gq < nplus && npp < nqq) || (gp >= nplus && npp > nqq);
+            }
+            if (rho || swap) {
+#pragma unroll
+                for (int k = 0; k < C::kRowsPerLane; ++k) {
+                    const int r = g + k * C::kLanesPerPair;
+                    double x = rp[r], z = rq[r];
+                    double u = wp[r], v = wq[r];
+                    if (rho) { rot_apply(x, z, t, rot); rot_apply(u, v, t, rot); }
+                    if (swap) {
+                        rp[r] = z; rq[r] = x; wp[r] = v; wq[r] = u;
+                    } else {
+                        rp[r] = x; rq[r] = z; wp[r] = u; wq[r] = v;
+                    }
+                }
+                changed = 1;
+            }
+            if (g == 0 && rho) {
+                ++my_rot;
+                ++sweep_rot;
+                if (rot.cs != 1.0) ++my_proper;
+            }
+            __syncthreads();
+        }
+        if (inner_sweeps > 1 && __syncthreads_count(sweep_rot) == 0) break;
+    }
+
+    // (6) V' and its flag to global memory; counters
+    const int any_change = __syncthreads_or(changed);
+    for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+        const int i = e % BB, j = e / BB;
+        vp[e] = A[i + j * C::kLd];
+    }
+    atomicAdd(&s_cnt[0], my_rot);
+    atomicAdd(&s_cnt[1], my_proper);
+    __syncthreads();
+    if (tid == 0) {
+        *vflag = any_change;
+        atomicAdd(&counters[kCntRot], (unsigned long long)s_cnt[0]);
+        atomicAdd(&counters[kCntProper], (unsigned long long)s_cnt[1]);
+        if (any_change) atomicAdd(&counters[kCntUpdated], 1ull);
+        if (s_brk) atomicAdd(&counters[kCntBreak], (unsigned long long)s_brk);
+        atomicMax(&counters[kCntOff], s_off);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Rows [r0, r0 + valid) of [A_P A_Q] := [A_P A_Q] V' (valid <= kUpdRows, a
+// multiple of 4).  X (column-major, ld kUpdRows) and V' (row-major by k,
+// ld BB+2) in shared memory; thread (rt, ct) owns a 4x4 output tile and sums
+// over k = 0..BB-1 in increasing order.  Units of one pair own disjoint rows,
+// so the result is written in place.
+template <int BB, typename T>
+__device__ __forceinline__ void update_unit(T *__restrict__ M, int ld, int r0, int valid, int P, int Q,
+                                            int b, const double *__restrict__ vp, T *X) {
+    using C = Cfg<BB>;
+    using T2 = typename Vec2<T>::type;
+    constexpr int RU = C::kUpdRows;
+    constexpr int WLD = BB + 2;
+    T *W = X + BB * RU;
+    for (int e = threadIdx.x; e < BB * BB; e += kUpdThreads) {
+        const int k = e % BB, c = e / BB;
+        W[k * WLD + c] = (T)vp[e];
+    }
+    for (int e = threadIdx.x; e < BB * RU / 2; e += kUpdThreads) {
+        const int r2 = e % (RU / 2), j = e / (RU / 2);
+        if (2 * r2 < valid)
+            reinterpret_cast<T2 *>(X + j * RU)[r2] =
+                reinterpret_cast<const T2 *>(M + (size_t)block_col(P, Q, b, j) * ld + r0)[r2];
+    }
+    __syncthreads();
+    const int rt = threadIdx.x % (RU / 4);
+    const int ct = threadIdx.x / (RU / 4);
+    if (4 * rt >= valid) return;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+#pragma unroll 4
+    for (int k = 0; k < BB; ++k) {
+        const T2 x01 = reinterpret_cast<const T2 *>(X + k * RU + 4 * rt)[0];
+        const T2 x23 = reinterpret_cast<const T2 *>(X + k * RU + 4 * rt)[1];
+        const T2 w01 = reinterpret_cast<const T2 *>(W + k * WLD + 4 * ct)[0];
+        const T2 w23 = reinterpret_cast<const T2 *>(W + k * WLD + 4 * ct)[1];
+        const T xv[4] = {x01.x, x01.y, x23.x, x23.y};
+        const T wv[4] = {w01.x, w01.y, w23.x, w23.y};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], wv[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        T2 *dst = reinterpret_cast<T2 *>(M + (size_t)block_col(P, Q, b, 4 * ct + j) * ld + r0 + 4 * rt);
+        T2 lo, hi;
+        lo.x = acc[0][j]; lo.y = acc[1][j];
+        hi.x = acc[2][j]; hi.y = acc[3][j];
+        dst[0] = lo;
+        dst[1] = hi;
+    }
+}
+
+}  // namespace jsvd

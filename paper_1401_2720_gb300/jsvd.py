@@ -56,7 +56,7 @@ _ctx: dict[int, ctypes.c_void_p] = {}
 EXPORTED = ["jsvd_default_opts", "jsvd_create", "jsvd_destroy", "jsvd_set_stream",
             "jsvd_last_error", "jsvd_status_string", "jsvd_dgesvj", "jsvd_dhsvj",
             "jsvd_pivot_table", "jsvd_rotation_params", "jsvd_profile", "jsvd_profile_read",
-            "jsvd_fp64_peak"]
+            "jsvd_fp64_peak", "jsvd_dgesvj_batched", "jsvd_dgesvj_backward"]
 
 
 def library():
@@ -84,6 +84,9 @@ def library():
             lib.jsvd_profile.argtypes = [P, I]
             lib.jsvd_profile_read.argtypes = [P, P, P, P, I]
             lib.jsvd_fp64_peak.argtypes = [P, D, P, P]
+            lib.jsvd_dgesvj_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P,
+                                                ctypes.POINTER(Opts), P]
+            lib.jsvd_dgesvj_backward.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -161,13 +164,13 @@ def svd(A: torch.Tensor, *, with_v: bool = True, return_info: bool = False, out=
     return (res + (dict(info.as_dict(), status=rc),)) if return_info else res
 
 
-def hsvd(G: torch.Tensor, n_plus: int, *, with_v: bool = True, return_info: bool = False, **kw):
+def hsvd(G: torch.Tensor, n_plus: int, *, with_v: bool = True, return_info: bool = False, out=None, **kw):
     """Hyperbolic SVD G = U diag(S) V^T, V^T J V = J, J = diag(I_{n_plus}, -I)."""
     m, n = G.shape
     if m < n:
         raise ValueError("hsvd needs m >= n")
     Gc, ldg = _colmajor(G)
-    U, S, V = _outputs(m, n, with_v, G.device)
+    U, S, V = out if out is not None else _outputs(m, n, with_v, G.device)
     opts = make_opts(**kw)
     info = Info()
     h = context(G.device.index)
@@ -233,3 +236,132 @@ def fp64_peak(seconds: float = 1.0, device: int | None = None) -> tuple[float, f
     if rc:
         _raise(rc, h)
     return a.value, b.value
+
+
+# ---------------------------------------------------------------------------
+# batches of matrices of uneven sizes (packed column-major buffers)
+
+class Packing:
+    """Element offsets of a batch of column-major matrices packed back to back:
+    A_i (m_i x n_i), U_i (m_i x n_i), S_i (n_i), V_i (n_i x n_i)."""
+
+    def __init__(self, ms, ns):
+        self.m = np.ascontiguousarray(ms, dtype=np.int32)
+        self.n = np.ascontiguousarray(ns, dtype=np.int32)
+        mn = self.m.astype(np.int64) * self.n
+        nn = self.n.astype(np.int64) ** 2
+        self.mn_off = np.concatenate([[0], np.cumsum(mn)[:-1]]).astype(np.int64)
+        self.n_off = np.concatenate([[0], np.cumsum(self.n.astype(np.int64))[:-1]]).astype(np.int64)
+        self.nn_off = np.concatenate([[0], np.cumsum(nn)[:-1]]).astype(np.int64)
+        self.mn_total = int(mn.sum())
+        self.n_total = int(self.n.sum())
+        self.nn_total = int(nn.sum())
+
+    def __len__(self):
+        return len(self.m)
+
+    def pack(self, mats, device) -> torch.Tensor:
+        """Column-major pack of a list of (m_i x n_i) tensors/arrays."""
+        parts = [torch.as_tensor(np.asarray(x) if not torch.is_tensor(x) else x).to(torch.float64).t().reshape(-1)
+                 for x in mats]
+        return torch.cat([p.to(device) for p in parts]) if parts else torch.empty(0, dtype=torch.float64, device=device)
+
+    def unpack_mn(self, buf):
+        return [buf[o:o + int(m) * int(n)].view(int(n), int(m)).t() for o, m, n in zip(self.mn_off, self.m, self.n)]
+
+    def unpack_n(self, buf):
+        return [buf[o:o + int(n)] for o, n in zip(self.n_off, self.n)]
+
+    def unpack_nn(self, buf):
+        return [buf[o:o + int(n) * int(n)].view(int(n), int(n)).t() for o, n in zip(self.nn_off, self.n)]
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def svd_batched_packed(pk: Packing, A: torch.Tensor, *, b=None, with_v: bool = True, return_info: bool = False,
+                       **kw):
+    """Batched SVD on packed buffers: returns packed (U, S, V) (+ infos)."""
+    dev = A.device
+    U = torch.empty(pk.mn_total, dtype=torch.float64, device=dev)
+    S = torch.empty(pk.n_total, dtype=torch.float64, device=dev)
+    V = torch.empty(pk.nn_total, dtype=torch.float64, device=dev) if with_v else None
+    bs = None if b is None else np.ascontiguousarray(np.broadcast_to(b, (len(pk),)), dtype=np.int32)
+    opts = make_opts(**kw)
+    infos = (Info * len(pk))()
+    h = context(dev.index)
+    rc = library().jsvd_dgesvj_batched(h, len(pk), _p(pk.m), _p(pk.n), _p(bs) if bs is not None else None,
+                                       A.data_ptr(), _p(pk.mn_off), S.data_ptr(), _p(pk.n_off), U.data_ptr(),
+                                       _p(pk.mn_off), V.data_ptr() if V is not None else None,
+                                       _p(pk.nn_off) if V is not None else None, ctypes.byref(opts), infos)
+    if rc not in (0, 1):
+        _raise(rc, h)
+    out = (U, S, V)
+    if return_info:
+        out = out + ([dict(i.as_dict()) for i in infos], rc)
+    return out
+
+
+def svd_backward_packed(pk: Packing, U, S, V, dU=None, dS=None, dV=None) -> torch.Tensor:
+    """Packed dA from packed U, S, V and cotangents (None = zero)."""
+    dA = torch.empty(pk.mn_total, dtype=torch.float64, device=U.device)
+    h = context(U.device.index)
+    ptr = lambda t: t.contiguous().data_ptr() if t is not None else None
+    rc = library().jsvd_dgesvj_backward(h, len(pk), _p(pk.m), _p(pk.n), U.data_ptr(), _p(pk.mn_off),
+                                        S.data_ptr(), _p(pk.n_off), V.data_ptr(), _p(pk.nn_off),
+                                        ptr(dU), ptr(dS), ptr(dV), dA.data_ptr(), _p(pk.mn_off))
+    if rc:
+        _raise(rc, h)
+    return dA
+
+
+class _BatchedSVD(torch.autograd.Function):
+    """Packed batched SVD with the library's adjoint as its backward."""
+
+    @staticmethod
+    def forward(ctx, A, pk, b, kw):
+        U, S, V = svd_batched_packed(pk, A.detach(), b=b, **kw)
+        ctx.pk = pk
+        ctx.save_for_backward(U, S, V)
+        return U, S, V
+
+    @staticmethod
+    def backward(ctx, dU, dS, dV):
+        U, S, V = ctx.saved_tensors
+        dA = svd_backward_packed(ctx.pk, U, S, V, dU, dS, dV)
+        return dA, None, None, None
+
+
+def svd_batched(mats, *, b=None, **kw):
+    """Differentiable batched SVD of a list of (m_i x n_i) float64 CUDA
+    tensors (m_i >= n_i): returns lists U_i, S_i, V_i (views of packed
+    buffers); gradients flow back to the inputs through the SVD adjoint."""
+    ms = [int(x.shape[0]) for x in mats]
+    ns = [int(x.shape[1]) for x in mats]
+    pk = Packing(ms, ns)
+    A = torch.cat([x.t().reshape(-1) for x in mats])
+    U, S, V = _BatchedSVD.apply(A, pk, b, kw)
+    return pk.unpack_mn(U), pk.unpack_n(S), pk.unpack_nn(V)
+
+
+class _SVD(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, kw):
+        U, S, V = svd(A.detach(), **kw)
+        ctx.save_for_backward(U, S, V)
+        return U, S, V
+
+    @staticmethod
+    def backward(ctx, dU, dS, dV):
+        U, S, V = ctx.saved_tensors
+        m, n = U.shape
+        pk = Packing([m], [n])
+        flat = lambda t: None if t is None else t.t().contiguous().reshape(-1)
+        dA = svd_backward_packed(pk, flat(U), S.contiguous(), flat(V), flat(dU), dS, flat(dV))
+        return dA.view(n, m).t(), None
+
+
+def svd_autograd(A: torch.Tensor, **kw):
+    """Differentiable single-matrix SVD (forward jsvd_dgesvj, backward the adjoint)."""
+    return _SVD.apply(A, kw)

@@ -136,3 +136,22 @@ def test_block_pstep_invariants():
 
     for P_, Q_ in tab[0]:
         assert off(G, P_, Q_) < off(A, P_, Q_)
+
+
+@pytest.mark.parametrize("mn", [(2, 2), (5, 5), (40, 17), (97, 33), (300, 75), (64, 1)])
+def test_block_method_with_identity_border(mn):
+    """Identity bordering to a multiple of 2b (border columns static): the
+    matrix columns' sigma equal LAPACK's, and the border rows of the matrix
+    columns stay exactly zero."""
+    m, n = mn
+    A = I.gaussian(m, n, seed=m + n) * (10.0 ** np.linspace(0, -3, n))[None, :]
+    B, bd, _ = O.bordered(A, 8)
+    r = O.block_svd(B, 8, strategy="modulus", border=bd)
+    assert r["converged"]
+    keep = np.ones(B.shape[1], bool)
+    keep[bd[0]:bd[1]] = False
+    s = np.sort(np.sqrt((r["G"][:, keep] ** 2).sum(0)))[::-1]
+    sl = np.linalg.svd(A, compute_uv=False)
+    assert np.max(np.abs(s - sl)) <= 50 * np.sqrt(max(n, 2)) * EPS * sl[0]
+    assert np.all(r["G"][m:, keep] == 0.0)
+    assert np.array_equal(r["G"][:, ~keep], B[:, ~keep])     # the border never moves
