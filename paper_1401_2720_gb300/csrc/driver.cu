@@ -121,11 +121,15 @@ __global__ void k_eye_f32(float *__restrict__ V, int ldv, int v_rows, int n_pad)
     }
 }
 
-// E := S - I (in place), n x n, ld n.
-__global__ void k_sub_eye(double *__restrict__ S, int n) {
+// E := J S - I (in place), n x n, ld n, J = diag(+1 x nplus, -1 x (n - nplus)).
+__global__ void k_jsub_eye(double *__restrict__ S, int n, int nplus) {
     const size_t total = (size_t)n * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
-        if (e % n == e / n) S[e] = S[e] - 1.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % n);
+        double v = r < nplus ? S[e] : -S[e];
+        if (r == (int)(e / n)) v -= 1.0;
+        S[e] = v;
+    }
 }
 
 // M := I - E/2 + (3/8) E^2 (into E2), the first terms of (I + E)^{-1/2}.
@@ -254,19 +258,27 @@ int jsvd_ctx::sync(const char *where) {
 }
 
 // Mixed precision, stage 2.  V32 (FP32, n x n inside an ld-v32 buffer) is
-// orthogonal to about the FP32 unit roundoff; its polar factor is
-//   Q = V32 (V32^T V32)^{-1/2} = V32 (I - E/2 + 3E^2/8 - ...),  E = V32^T V32 - I,
-// and with ||E|| ~ 1e-6 the truncation error ~||E||^3 is below the FP64 unit
-// roundoff.  Then G := G Q and V := Q, all in FP64.
-int jsvd_ctx::polar_and_apply(double *G, int ldg, int n, const float *V32, int ldv32, double *V, int ldv) {
+// J-orthogonal (orthogonal for the SVD, J = I) to about the FP32 unit
+// roundoff.  Its J-polar factor
+//   Q = V32 M^{-1/2},  M = J V32^T J V32 = I + E,
+// is exactly J-orthogonal (Q^T J Q = J), and for the SVD it is the polar
+// factor.  With ||E|| ~ 1e-6 the series (I + E)^{-1/2} = I - E/2 + 3E^2/8 - ...
+// truncated after E^2 leaves ~||E||^3, below the FP64 unit roundoff.  Then
+// G := G Q and V := Q, all in FP64.  Columns < nplus have J = +1.
+int jsvd_ctx::polar_and_apply(double *G, int ldg, int n, int nplus, const float *V32, int ldv32, double *V,
+                              int ldv) {
     int rc;
     const size_t nn = (size_t)n * n;
     if ((rc = ensure(tmp_a, sizeof(double) * nn))) return rc;
     if ((rc = ensure(tmp_b, sizeof(double) * nn))) return rc;
     if ((rc = ensure(tmp_g, sizeof(double) * (size_t)ldg * n))) return rc;
     double *E = (double *)tmp_a.ptr, *E2 = (double *)tmp_b.ptr, *G2 = (double *)tmp_g.ptr;
-    gemm(true, false, Elt::F32, Elt::F32, n, n, n, 1.0, V32, ldv32, V32, ldv32, 0.0, E, n, stream);
-    k_sub_eye<<<1024, 256, 0, stream>>>(E, n);
+    // S = V32^T J V32 = V32(+)^T V32(+) - V32(-)^T V32(-)  (row blocks of V32)
+    gemm(true, false, Elt::F32, Elt::F32, n, n, nplus, 1.0, V32, ldv32, V32, ldv32, 0.0, E, n, stream);
+    if (nplus < n)
+        gemm(true, false, Elt::F32, Elt::F32, n, n, n - nplus, -1.0, V32 + nplus, ldv32, V32 + nplus, ldv32, 1.0,
+             E, n, stream);
+    k_jsub_eye<<<1024, 256, 0, stream>>>(E, n, nplus);
     gemm(false, false, Elt::F64, Elt::F64, n, n, n, 1.0, E, n, E, n, 0.0, E2, n, stream);
     k_polar_combine<<<1024, 256, 0, stream>>>(E, E2, n);
     gemm(false, false, Elt::F32, Elt::F64, n, n, n, 1.0, V32, ldv32, E2, n, 0.0, V, ldv, stream);
@@ -448,7 +460,7 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
         if ((rc = sweep_loop(o.max_sweeps, &low_done, &low_conv))) return rc;
         inf.sweeps_low = low_done;
         // Stage 2: Q = polar factor of V32 in FP64, G := G Q, V := Q.
-        if ((rc = polar_and_apply(G, g_rows, n_pad, V32, v_rows, V, v_rows))) return rc;
+        if ((rc = polar_and_apply(G, g_rows, n_pad, nplus_w, V32, v_rows, V, v_rows))) return rc;
     }
     a.G = G; a.V = want_v ? V : nullptr; a.fp32 = 0; a.eps = kEps;
     int converged = 0, sweeps = 0;

@@ -42,7 +42,7 @@ struct jsvd_ctx {
     void set_error(const char *where, cudaError_t e);
     int check(const char *where);
     int sync(const char *where);
-    int polar_and_apply(double *G, int ldg, int n, const float *V32, int ldv32, double *V, int ldv);
+    int polar_and_apply(double *G, int ldg, int n, int nplus, const float *V32, int ldv32, double *V, int ldv);
     int ensure(Buffer &buf, size_t bytes);
     int table(int strategy, int n, const int **dev);
     int inner_table(int strategy, int BB, const unsigned char **dev);

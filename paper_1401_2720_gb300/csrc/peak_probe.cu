@@ -14,16 +14,21 @@ namespace {
 constexpr int kChains = 16;   // independent FMA chains per thread
 constexpr int kMma = 8;       // independent mma accumulators per warp
 
+// Each chain has its own multiplier and addend registers, as the operands of
+// a GEMM inner loop do (shared operand registers throttle operand delivery).
 __global__ void probe_dfma(double *out, int iters) {
-    double a[kChains];
+    double a[kChains], bm[kChains], cm[kChains];
 #pragma unroll
-    for (int j = 0; j < kChains; ++j) a[j] = 1e-3 * threadIdx.x + j;
-    const double b = 0.9999999, c = 1e-7;
+    for (int j = 0; j < kChains; ++j) {
+        a[j] = 1e-3 * threadIdx.x + j;
+        bm[j] = 0.9999999 - 1e-9 * j;
+        cm[j] = 1e-7 * (j + 1);
+    }
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int r = 0; r < 8; ++r)
 #pragma unroll
-            for (int j = 0; j < kChains; ++j) a[j] = __fma_rn(a[j], b, c);
+            for (int j = 0; j < kChains; ++j) a[j] = __fma_rn(a[j], bm[(j + r) % kChains], cm[(j + 3 * r) % kChains]);
     }
     double s = 0.0;
 #pragma unroll
@@ -32,7 +37,12 @@ __global__ void probe_dfma(double *out, int iters) {
 }
 
 __global__ void probe_dmma(double *out, int iters) {
-    const double a = 1e-3 * (threadIdx.x & 7), b = 0.5;
+    double av[kMma], bv[kMma];
+#pragma unroll
+    for (int j = 0; j < kMma; ++j) {
+        av[j] = 1e-3 * ((threadIdx.x + j) & 7);
+        bv[j] = 0.5 - 1e-3 * j;
+    }
     double c[kMma][2];
 #pragma unroll
     for (int j = 0; j < kMma; ++j) c[j][0] = c[j][1] = 0.0;
@@ -41,7 +51,7 @@ __global__ void probe_dmma(double *out, int iters) {
         for (int j = 0; j < kMma; ++j)
             asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
                          : "+d"(c[j][0]), "+d"(c[j][1])
-                         : "d"(a), "d"(b));
+                         : "d"(av[j]), "d"(bv[(j + 3) % kMma]));
     }
     double s = 0.0;
 #pragma unroll

@@ -32,8 +32,10 @@ constexpr int kUpdThreads = 256;   // 4x4 output tiles per thread
 
 template <int BB> struct Cfg {
     static constexpr int kPairsInner = BB / 2;
-    static constexpr int kLanesPerPair = 8;
-    static constexpr int kJacThreads = kPairsInner * kLanesPerPair;   // 4*BB
+    // 128 threads for every BB: one warp per SM sub-partition (each has its
+    // own FP64 unit), with the fewest lanes per inner pair that fill them
+    static constexpr int kLanesPerPair = 256 / BB;
+    static constexpr int kJacThreads = kPairsInner * kLanesPerPair;   // 128
     static constexpr int kRowsPerLane = BB / kLanesPerPair;
     static constexpr int kLd = BB + 1;                                // smem ld for R, V'
     static constexpr int kPacked = BB * (BB + 1) / 2;
@@ -110,8 +112,9 @@ __device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int 
 // inner table ((BB-1) x BB/2 pairs of bytes).
 //   A: H (lower) -> L by Cholesky -> V' (= I, then rotated)
 //   B: R = L^T (upper), rotated in the inner sweeps
-// Inner p-step: pair y of the inner table is handled by the 8-lane group y;
-// lane g of the group owns rows g, g+8, ... of both columns in R and V'.
+// Inner p-step: pair y of the inner table is handled by the lane group y
+// (256/BB lanes); lane g of the group owns rows g, g + 256/BB, ... of both
+// columns in R and V'.
 // Writes V' (column-major, BB x BB) to vp and "V' != I" to *vflag; adds the
 // rotation counts to counters[].  Global columns in [bord_lo, bord_hi) are the
 // identity border: they are exactly orthogonal to everything, and they are
