@@ -39,6 +39,7 @@ extern "C" {
 #define JSVD_ERR_ALLOC        4  /* workspace allocation failed */
 #define JSVD_ERR_UNSUPPORTED  5  /* option combination not supported */
 #define JSVD_ERR_TIMEOUT      6  /* a bounded device-side wait gave up */
+#define JSVD_ERR_TOO_LARGE    7  /* jsvd_dgesvj_noalloc: problem exceeds its static scratch */
 
 /* ---- pivot strategies (Sec. 3) ---------------------------------------- */
 #define JSVD_STRAT_MODULUS   0  /* modulus ordering: odd-order modulus completed to even order */
@@ -146,6 +147,29 @@ int jsvd_dgesvj_backward(jsvd_ctx_t ctx, int batch, const int *m, const int *n, 
                          const long long *u_off, const double *S, const long long *s_off, const double *V,
                          const long long *v_off, const double *dU, const double *dS, const double *dV,
                          double *dA, const long long *a_off);
+
+/* jsvd_dgesvj for callers that cannot allocate device memory (code that runs
+ * while a CUDA graph is being captured, a framework whose memory pool owns all
+ * device memory, a process under a cudaMalloc cap).  The paper has no
+ * counterpart.  Same arguments and results as jsvd_dgesvj, FP64 only
+ * (opts->precision must be JSVD_PREC_FP64), without a context: the work runs
+ * on `stream` (a cudaStream_t, NULL = legacy default stream) of the current
+ * device.
+ * All scratch lives in one static __device__ array of 64 MiB inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits; the call makes no cudaMalloc, cudaMallocHost or cudaFree and uses no
+ * allocating library routine (only a few small host-side C++ vectors).  A
+ * problem whose scratch (about 8 * (m+k)*n_pad + 8 * n_pad^2 bytes plus the
+ * Gram partials; n_pad = n rounded up to a multiple of 2b) exceeds the array
+ * is rejected with JSVD_ERR_TOO_LARGE before any GPU work (m = n = 1024 fits,
+ * 2048 does not).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * contents behind; the solver initialises everything it reads.  Calls whose
+ * GPU work overlaps (two streams, two host threads) race on the array.      */
+int jsvd_dgesvj_noalloc(int m, int n, const double *A, int lda, double *S, double *U, int ldu,
+                        double *V, int ldv, const jsvd_opts *opts, jsvd_info *info, void *stream);
 
 /* The block p-strategy table of order nblocks (even, >= 2) for `strategy`:
  * out_pairs (host, 2*(nblocks-1)*(nblocks/2) ints) receives, p-step by p-step,

@@ -586,6 +586,7 @@ const char *jsvd_status_string(int s) {
         case JSVD_ERR_ALLOC: return "workspace allocation failed";
         case JSVD_ERR_UNSUPPORTED: return "unsupported option";
         case JSVD_ERR_TIMEOUT: return "bounded device wait gave up";
+        case JSVD_ERR_TOO_LARGE: return "problem exceeds the static scratch of the no-allocation entry point";
         default: return s < 0 ? "invalid argument" : "unknown status";
     }
 }

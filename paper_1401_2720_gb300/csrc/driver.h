@@ -38,12 +38,12 @@ struct jsvd_ctx {
     std::vector<cudaEvent_t> events;  // 4 per p-step of one sweep
     int ensure_events(size_t count);
 
-    ~jsvd_ctx();
+    virtual ~jsvd_ctx();
     void set_error(const char *where, cudaError_t e);
     int check(const char *where);
     int sync(const char *where);
     int polar_and_apply(double *G, int ldg, int n, int nplus, const float *V32, int ldv32, double *V, int ldv);
-    int ensure(Buffer &buf, size_t bytes);
+    virtual int ensure(Buffer &buf, size_t bytes);
     int table(int strategy, int n, const int **dev);
     int inner_table(int strategy, int BB, const unsigned char **dev);
     int solve_batched(int batch, const int *m, const int *n, const int *b, const double *A,

@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libjsvd.so")
 STRATEGIES = {"modulus": 0, "R": 1, "C": 2, "rR": 3, "rC": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 STATUS = {0: "success", 1: "not converged", 2: "non-finite input", 3: "CUDA error",
-          4: "allocation failed", 5: "unsupported", 6: "device wait timed out"}
+          4: "allocation failed", 5: "unsupported", 6: "device wait timed out",
+          7: "too large for the no-allocation entry point"}
 
 
 class JsvdError(RuntimeError):
@@ -56,7 +57,8 @@ _ctx: dict[int, ctypes.c_void_p] = {}
 EXPORTED = ["jsvd_default_opts", "jsvd_create", "jsvd_destroy", "jsvd_set_stream",
             "jsvd_last_error", "jsvd_status_string", "jsvd_dgesvj", "jsvd_dhsvj",
             "jsvd_pivot_table", "jsvd_rotation_params", "jsvd_profile", "jsvd_profile_read",
-            "jsvd_fp64_peak", "jsvd_dgesvj_batched", "jsvd_dgesvj_backward"]
+            "jsvd_fp64_peak", "jsvd_dgesvj_batched", "jsvd_dgesvj_backward",
+            "jsvd_dgesvj_noalloc"]
 
 
 def library():
@@ -87,6 +89,8 @@ def library():
             lib.jsvd_dgesvj_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P,
                                                 ctypes.POINTER(Opts), P]
             lib.jsvd_dgesvj_backward.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P, P, P]
+            lib.jsvd_dgesvj_noalloc.argtypes = [I, I, P, I, P, P, I, P, I, ctypes.POINTER(Opts),
+                                                ctypes.POINTER(Info), P]
             _lib = lib
     return _lib
 
@@ -365,3 +369,22 @@ class _SVD(torch.autograd.Function):
 def svd_autograd(A: torch.Tensor, **kw):
     """Differentiable single-matrix SVD (forward jsvd_dgesvj, backward the adjoint)."""
     return _SVD.apply(A, kw)
+
+
+def svd_noalloc(A: torch.Tensor, *, out=None, return_info: bool = False, **kw):
+    """jsvd_dgesvj_noalloc: the FP64 SVD with all scratch in the library's
+    static device array (no device allocation by the library; the outputs are
+    allocated here unless `out` is given)."""
+    m, n = A.shape
+    Ac, lda = _colmajor(A)
+    U, S, V = out if out is not None else _outputs(m, n, True, A.device)
+    opts = make_opts(**kw)
+    info = Info()
+    stream = ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream)
+    rc = library().jsvd_dgesvj_noalloc(m, n, Ac.data_ptr(), lda, S.data_ptr(), U.data_ptr(), U.stride(1),
+                                       V.data_ptr() if V is not None else None, V.stride(1) if V is not None else 1,
+                                       ctypes.byref(opts), ctypes.byref(info), stream)
+    if rc not in (0, 1):
+        raise JsvdError(rc, "jsvd_dgesvj_noalloc failed")
+    res = (U, S, V)
+    return (res + (dict(info.as_dict(), status=rc),)) if return_info else res
