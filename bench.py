@@ -32,10 +32,16 @@ METRIC = "FP64 Jacobi SVD s/matrix at 8192²; TFLOP/s vs DMMA peak; mixed vs pla
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL_BF16_TF = 2250.0
 NOMINAL_FP64_TF = 1.25
+# FP64 pipe of a GB300: 152 SMs x 4 sub-partitions, one DFMA warp instruction
+# (32 lanes x 2 flop) per 64 cycles per sub-partition = 608 flop per cycle
+FP64_FLOP_PER_CYCLE = 152 * 4 * 32 * 2 // 64
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from an ncu capture of the current kernel build (None until taken).
-TRAFFIC_PER_LAUNCH: dict = {}
+# dram__bytes_read.sum + dram__bytes_write.sum of one block_update<64, double>
+# launch (ncu, 4096x4096 graded, b = 32, every pair updated) divided by the
+# (pair, row) units it processed: 477.9 MB / (64 pairs x 8192 rows).  The
+# traffic grows in proportion to the units, so a launch's traffic is this
+# figure times its units (algorithmic: 1024 B per unit, read + write).
+UPDATE_BYTES_PER_PAIR_ROW = 477.94e6 / (64 * 8192)
 
 WORKLOADS = {
     # name: (m, n, generator, description)
@@ -349,21 +355,31 @@ def run_gpu(args) -> None:
     # ---- roofline of the dominant kernel ---------------------------------------
     flops_total = sum(v[2] for v in prof.values())
     dom = max(("gram", "jacobi", "update"), key=lambda c: prof[c][0])
+    last_b = infos[-1]["b"]
     d_ms, d_launch, d_flops = prof[dom]
     derived, derived_src = fp64_peak_tflops(sustained=True)
-    peak = max(peak_dmma, peak_dfma)
+    sm_mhz = clk["sm_mhz"] if clk else 2070.0
+    peak = FP64_FLOP_PER_CYCLE * sm_mhz * 1e6 / 1e12
     achieved = d_flops / (d_ms * 1e-3) / 1e12 if d_ms > 0 else 0.0
-    traffic = TRAFFIC_PER_LAUNCH.get((args.workload, dom))
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    traffic = None
+    if dom == "update" and d_launch:
+        # ncu: 912 B of DRAM traffic per (pair, row) of block_update<64, double>
+        bb = 2 * last_b
+        traffic = UPDATE_BYTES_PER_PAIR_ROW * (d_flops / (2.0 * bb * bb)) / d_launch
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "traffic": traffic,
                 "kernel": {"gram": "gram_partial", "jacobi": "pair_jacobi", "update": "block_update"}[dom],
                 "launches": d_launch,
-                "peak_source": (f"FP64 peak measured in this run by the library's probe: mma.sync m8n8k4 "
-                                f"{peak_dmma:.3f}, DFMA {peak_dfma:.3f} TFLOP/s (of measured)"),
+                "peak_source": (f"FP64 pipe: {FP64_FLOP_PER_CYCLE} flop/cycle (152 SMs x 4 sub-partitions x one "
+                                f"DFMA warp instruction per 64 cycles, the sm__inst_executed_pipe_fp64 peak) x "
+                                f"median SM clock {sm_mhz:.0f} MHz in the timed region; in-run probes: DMMA "
+                                f"{peak_dmma:.3f}, DFMA {peak_dfma:.3f} TFLOP/s"),
                 "peak_derived": {"value": derived, "source": derived_src}}
     kernels = {c: {"ms": prof[c][0], "launches": prof[c][1], "tflops": (prof[c][2] / (prof[c][0] * 1e-3) / 1e12)
                    if prof[c][0] > 0 else None, "share": prof[c][0] / ms_total if ms_total else None}
-               for c in ("gram", "jacobi", "update")}
+               for c in ("gram", "jacobi", "update", "update_v")}
+    kernels["update_v"]["note"] = ("V update on the low-priority side stream: it runs in the main stream's gaps, "
+                                   "so its event time includes waiting for SMs and overlaps the other classes")
 
     cpu = None
     mixed_report = None

@@ -190,17 +190,20 @@ int jsvd_rotation_params(jsvd_ctx_t ctx, int count, const double *hpp,
 
 /* ---- instrumentation ---------------------------------------------------
  * Kernel classes: 0 = Gram partials, 1 = per-pair Cholesky + inner sweep,
- * 2 = block update (Eq. (2.9)), 3 = everything else (bordering copy, V = I,
- * column norms, output assembly, mixed-precision and batched kernels).
+ * 2 = block update (Eq. (2.9)) on the solve's main stream (G, or G and V when
+ * there is no side stream), 3 = update of V on the side stream (it runs in the
+ * gaps of the main stream, so its event time includes waiting for SMs),
+ * 4 = everything else (bordering copy, V = I, column norms, output assembly,
+ * mixed-precision, batched and adjoint kernels).
  * jsvd_profile(ctx, 1) clears the tallies and starts timing: every launch of
- * a class-0..2 kernel is then bracketed by CUDA events recorded on the
- * context's stream and the elapsed times are summed at each sweep boundary.
+ * a class-0..3 kernel is then bracketed by CUDA events recorded on the stream
+ * it runs on and the elapsed times are summed at each sweep boundary.
  * Launch counts and algorithmic FLOP counts are tallied whether or not
  * timing is on (cleared by jsvd_profile).  jsvd_profile_read copies ms[i],
- * launches[i] and flops[i] for i < nclass (nclass <= 4); any pointer may be
+ * launches[i] and flops[i] for i < nclass (nclass <= 5); any pointer may be
  * NULL.  Algorithmic FLOPs per pivot block pair with bb = 2b: Gram
- * m*bb*(bb+1), inner sweep 9*bb*bb*(bb-1) + bb^3/3, update 2*(m+n)*bb*bb
- * (only pairs with V' != I), with the caller's m and n.                     */
+ * m*bb*(bb+1), inner sweep 9*bb*bb*(bb-1) + bb^3/3, update 2*m*bb*bb for G
+ * and 2*n*bb*bb for V (only pairs with V' != I), with the caller's m, n.     */
 int jsvd_profile(jsvd_ctx_t ctx, int enable);
 int jsvd_profile_read(jsvd_ctx_t ctx, double *ms, long long *launches, double *flops, int nclass);
 

@@ -153,10 +153,10 @@ int jsvd_ctx::backward(int batch, const int *m, const int *n, const double *U, c
     k_adj_scale<<<blocks, 256, 0, stream>>>(dm, batch, dstart + batch, mn_tot, S, dU, W);
     gemm_grouped(false, false, Elt::F64, Elt::F64, dd + d1.size(), (int)d2.size(), t2, stream);
     gemm_grouped(false, true, Elt::F64, Elt::F64, dd + d1.size() + d2.size(), (int)d3.size(), t3, stream);
-    prof_launches[3] += (d1.empty() ? 0 : 1) + 4;
+    prof_launches[4] += (d1.empty() ? 0 : 1) + 4;
     double fl = 0.0;
     for (auto &M : mats) fl += 6.0 * M.m * (double)M.n * M.n + 2.0 * (double)M.n * M.n * M.n;
-    prof_flops[3] += fl;
+    prof_flops[4] += fl;
     if ((rc = check("adjoint"))) return rc;
     // the host descriptor vectors must outlive the async copies
     return sync("adjoint");

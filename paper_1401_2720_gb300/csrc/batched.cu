@@ -534,7 +534,7 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         if (profiling) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, events[0], events[1]);
-            prof_ms[3] += ms;
+            prof_ms[4] += ms;
         }
     } while (0);
     if (exec) cudaGraphExecDestroy(exec);
@@ -555,11 +555,11 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         return JSVD_ERR_NONFINITE;
     }
     int all_conv = 1;
-    prof_launches[3] += 3 + (long long)misc[0] * ((long long)plan.size() + 1);
+    prof_launches[4] += 3 + (long long)misc[0] * ((long long)plan.size() + 1);
     for (int i = 0; i < batch; ++i) {
         const int BB = 2 * mats[i].b;
         const double bbd = BB;
-        prof_flops[3] += (double)st[i].sweeps * (mats[i].nb - 1) * mats[i].npairs *
+        prof_flops[4] += (double)st[i].sweeps * (mats[i].nb - 1) * mats[i].npairs *
                              ((double)mats[i].m * bbd * (bbd + 1.0) + 9.0 * bbd * bbd * (bbd - 1.0) + bbd * bbd * bbd / 3.0) +
                          (double)st[i].updated * 2.0 * ((double)mats[i].m + (Vo ? (double)mats[i].n : 0.0)) * bbd * bbd;
         all_conv &= st[i].converged;

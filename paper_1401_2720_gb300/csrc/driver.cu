@@ -237,6 +237,24 @@ jsvd_ctx::~jsvd_ctx() {
         if (kv.second.ptr) cudaFree(kv.second.ptr);
     if (host_counters) cudaFreeHost(host_counters);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaEvent_t e : ring_events) cudaEventDestroy(e);
+    if (vstream) cudaStreamDestroy(vstream);
+    if (mstream) cudaStreamDestroy(mstream);
+}
+
+int jsvd_ctx::ensure_side_stream() {
+    if (!vstream) {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (cudaStreamCreateWithPriority(&mstream, cudaStreamNonBlocking, greatest) != cudaSuccess)
+            return check("main stream");
+        if (cudaStreamCreateWithPriority(&vstream, cudaStreamNonBlocking, least) != cudaSuccess)
+            return check("side stream");
+        ring_events.resize(2 * kVRing + 2);
+        for (auto &e : ring_events)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return check("ring events");
+    }
+    return 0;
 }
 
 int jsvd_ctx::ensure_events(size_t count) {
@@ -284,9 +302,9 @@ int jsvd_ctx::polar_and_apply(double *G, int ldg, int n, int nplus, const float 
     gemm(false, false, Elt::F32, Elt::F64, n, n, n, 1.0, V32, ldv32, E2, n, 0.0, V, ldv, stream);
     gemm(false, false, Elt::F64, Elt::F64, ldg, n, n, 1.0, G, ldg, V, ldv, 0.0, G2, ldg, stream);
     cudaMemcpyAsync(G, G2, sizeof(double) * (size_t)ldg * n, cudaMemcpyDeviceToDevice, stream);
-    prof_launches[3] += 6;
+    prof_launches[4] += 6;
     const double nd = (double)n;
-    prof_flops[3] += 2.0 * nd * nd * nd * 3.0 + 2.0 * (double)ldg * nd * nd;
+    prof_flops[4] += 2.0 * nd * nd * nd * 3.0 + 2.0 * (double)ldg * nd * nd;
     return check("polar");
 }
 
@@ -306,9 +324,29 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double *S, double *U,
-                    int ldu, double *Vout, int ldv, const jsvd_opts *opts_in, jsvd_info *info,
-                    bool hyperbolic) {
+// The solve runs on a high-priority stream of the library (the V updates on a
+// low-priority side stream fill its gaps), ordered after the caller's earlier
+// work on the context stream and before its later work.
+int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double *S, double *U, int ldu,
+                    double *Vout, int ldv, const jsvd_opts *opts_in, jsvd_info *info, bool hyperbolic) {
+    if (!side_streams)
+        return solve_on_stream(m, n, nplus_in, A, lda, S, U, ldu, Vout, ldv, opts_in, info, hyperbolic);
+    int rc = ensure_side_stream();
+    if (rc) return rc;
+    cudaStream_t user = stream;
+    cudaEventRecord(ring_events[2 * kVRing + 1], user);
+    cudaStreamWaitEvent(mstream, ring_events[2 * kVRing + 1], 0);
+    stream = mstream;
+    rc = solve_on_stream(m, n, nplus_in, A, lda, S, U, ldu, Vout, ldv, opts_in, info, hyperbolic);
+    cudaEventRecord(ring_events[2 * kVRing + 1], mstream);
+    cudaStreamWaitEvent(user, ring_events[2 * kVRing + 1], 0);
+    stream = user;
+    return rc;
+}
+
+int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int lda, double *S, double *U,
+                              int ldu, double *Vout, int ldv, const jsvd_opts *opts_in, jsvd_info *info,
+                              bool hyperbolic) {
     jsvd_opts o;
     jsvd_default_opts(&o);
     if (opts_in) o = *opts_in;
@@ -345,8 +383,10 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
     if ((rc = ensure(g, sizeof(double) * (size_t)g_rows * n_pad))) return rc;
     if ((rc = ensure(v, sizeof(double) * (size_t)v_rows * n_pad))) return rc;
     if ((rc = ensure(part, sizeof(double) * (size_t)npairs * g_chunks * (BB * (BB + 1) / 2)))) return rc;
-    if ((rc = ensure(vprime, sizeof(double) * (size_t)npairs * BB * BB))) return rc;
-    if ((rc = ensure(vflag, sizeof(int) * (size_t)npairs))) return rc;
+    const int ring = side_streams ? kVRing : 1;
+    if ((rc = ensure(vprime, sizeof(double) * (size_t)npairs * BB * BB * ring))) return rc;
+    if ((rc = ensure(vflag, sizeof(int) * (size_t)npairs * ring))) return rc;
+    if (side_streams && (rc = ensure_side_stream())) return rc;
     if ((rc = ensure(counters, sizeof(unsigned long long) * kCntSize))) return rc;
     if ((rc = ensure(sigma, sizeof(double) * (size_t)n_pad))) return rc;
     if ((rc = ensure(border, sizeof(int) * (size_t)n_pad))) return rc;
@@ -369,12 +409,12 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
 
     cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
     k_init_g<<<1024, 256, 0, stream>>>(A, lda, m, n, ins, k, G, g_rows, g_rows, n_pad, cnt + kCntErr);
-    prof_launches[3] += 1;
+    prof_launches[4] += 1;
     if (want_v) {
         k_eye<<<1024, 256, 0, stream>>>(V, v_rows, v_rows, n_pad);
-        prof_launches[3] += 1;
+        prof_launches[4] += 1;
     }
-    if (profiling && (rc = ensure_events(4 * (size_t)(nb - 1)))) return rc;
+    if (profiling && (rc = ensure_events(6 * (size_t)(nb - 1)))) return rc;
     if ((rc = check("init"))) return rc;
     cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize, cudaMemcpyDeviceToHost, stream);
     if ((rc = sync("init"))) return rc;
@@ -396,7 +436,8 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
     const double bbd = (double)BB;
     const double fl_gram = (double)npairs * m * bbd * (bbd + 1.0);
     const double fl_jac = (double)npairs * (9.0 * bbd * bbd * (bbd - 1.0) + bbd * bbd * bbd / 3.0);
-    const double fl_upd_pair = 2.0 * ((double)m + (want_v ? (double)n : 0.0)) * bbd * bbd;
+    const double fl_upd_g_pair = 2.0 * (double)m * bbd * bbd;
+    const double fl_upd_v_pair = want_v ? 2.0 * (double)n * bbd * bbd : 0.0;
 
     jsvd_info inf{};
     inf.b = b;
@@ -406,13 +447,44 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
         *conv = 0;
         while (*done < limit) {
             cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
+            const bool side = side_streams && a.V != nullptr;
             for (int s = 0; s < nb - 1; ++s) {
+                // V' and its flags rotate through a ring of slots so that the V
+                // update of step s can still read its slot while steps s+1.. run
+                const int slot = s % ring;
                 a.step = s;
-                launch_pstep_fp64(BB, a, stream, profiling ? &events[4 * (size_t)s] : nullptr);
+                a.vprime = (double *)vprime.ptr + (size_t)slot * npairs * BB * BB;
+                a.vflag = (int *)vflag.ptr + (size_t)slot * npairs;
+                cudaEvent_t *ev = profiling ? &events[6 * (size_t)s] : nullptr;
+                if (side && s >= ring) cudaStreamWaitEvent(stream, ring_events[ring + slot], 0);
+                if (ev) cudaEventRecord(ev[0], stream);
+                launch_phase(BB, Phase::Gram, a, stream);
+                if (ev) cudaEventRecord(ev[1], stream);
+                launch_phase(BB, Phase::Jacobi, a, stream);
+                if (ev) cudaEventRecord(ev[2], stream);
+                if (side) {
+                    // [V_p V_q] := [V_p V_q] V' does not feed the next Gram: it runs on
+                    // the side stream, overlapping the next steps' Gram and Jacobi
+                    cudaEventRecord(ring_events[slot], stream);
+                    cudaStreamWaitEvent(vstream, ring_events[slot], 0);
+                    if (ev) cudaEventRecord(ev[4], vstream);
+                    launch_phase(BB, Phase::UpdateV, a, vstream);
+                    if (ev) cudaEventRecord(ev[5], vstream);
+                    cudaEventRecord(ring_events[ring + slot], vstream);
+                    launch_phase(BB, Phase::UpdateG, a, stream);
+                } else {
+                    launch_phase(BB, Phase::UpdateGV, a, stream);
+                }
+                if (ev) cudaEventRecord(ev[3], stream);
+            }
+            if (side) {
+                cudaEventRecord(ring_events[2 * ring], vstream);
+                cudaStreamWaitEvent(stream, ring_events[2 * ring], 0);
             }
             prof_launches[0] += nb - 1;
             prof_launches[1] += nb - 1;
             prof_launches[2] += nb - 1;
+            if (side) prof_launches[3] += nb - 1;
             if (int r = check("p-step")) return r;
             cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize,
                             cudaMemcpyDeviceToHost, stream);
@@ -420,14 +492,25 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
             ++*done;
             prof_flops[0] += fl_gram * (nb - 1);
             prof_flops[1] += fl_jac * (nb - 1);
-            prof_flops[2] += fl_upd_pair * (double)host_counters[kCntUpdated];
+            if (side) {
+                prof_flops[2] += fl_upd_g_pair * (double)host_counters[kCntUpdated];
+                prof_flops[3] += fl_upd_v_pair * (double)host_counters[kCntUpdated];
+            } else {
+                prof_flops[2] += (fl_upd_g_pair + fl_upd_v_pair) * (double)host_counters[kCntUpdated];
+            }
             if (profiling) {
-                for (int s = 0; s < nb - 1; ++s)
+                for (int s = 0; s < nb - 1; ++s) {
+                    const cudaEvent_t *ev = &events[6 * (size_t)s];
+                    float ms = 0.f;
                     for (int c = 0; c < 3; ++c) {
-                        float ms = 0.f;
-                        cudaEventElapsedTime(&ms, events[4 * (size_t)s + c], events[4 * (size_t)s + c + 1]);
+                        cudaEventElapsedTime(&ms, ev[c], ev[c + 1]);
                         prof_ms[c] += ms;
                     }
+                    if (side) {
+                        cudaEventElapsedTime(&ms, ev[4], ev[5]);
+                        prof_ms[3] += ms;
+                    }
+                }
             }
             inf.rotations += (long long)host_counters[kCntRot];
             inf.proper_rotations += (long long)host_counters[kCntProper];
@@ -454,7 +537,7 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
         float *G32 = (float *)g32.ptr, *V32 = (float *)v32.ptr;
         k_to_f32<<<1024, 256, 0, stream>>>(G, G32, (size_t)g_rows * n_pad);
         k_eye_f32<<<1024, 256, 0, stream>>>(V32, v_rows, v_rows, n_pad);
-        prof_launches[3] += 2;
+        prof_launches[4] += 2;
         a.G = G32; a.V = V32; a.fp32 = 1; a.eps = 0x1p-24;
         int low_done = 0, low_conv = 0;
         if ((rc = sweep_loop(o.max_sweeps, &low_done, &low_conv))) return rc;
@@ -472,7 +555,7 @@ int jsvd_ctx::solve(int m, int n, int nplus_in, const double *A, int lda, double
     double *dsig = (double *)sigma.ptr;
     int *dbd = (int *)border.ptr;
     k_colnorms<<<(n_pad * 32 + 255) / 256, 256, 0, stream>>>(G, g_rows, m_b, m, k, n_pad, dsig, dbd);
-    prof_launches[3] += 2;  // column norms and output assembly
+    prof_launches[4] += 2;  // column norms and output assembly
     if ((rc = check("colnorms"))) return rc;
     std::vector<double> hs(n_pad);
     std::vector<int> hb(n_pad);
@@ -556,7 +639,7 @@ int jsvd_set_stream(jsvd_ctx_t ctx, void *stream) {
 int jsvd_profile(jsvd_ctx_t ctx, int enable) {
     if (!ctx) return -1;
     ctx->profiling = enable != 0;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < jsvd_ctx::kClasses; ++i) {
         ctx->prof_ms[i] = 0.0;
         ctx->prof_launches[i] = 0;
         ctx->prof_flops[i] = 0.0;
@@ -566,7 +649,7 @@ int jsvd_profile(jsvd_ctx_t ctx, int enable) {
 
 int jsvd_profile_read(jsvd_ctx_t ctx, double *ms, long long *launches, double *flops, int nclass) {
     if (!ctx) return -1;
-    if (nclass < 0 || nclass > 4) return -5;
+    if (nclass < 0 || nclass > jsvd_ctx::kClasses) return -5;
     for (int i = 0; i < nclass; ++i) {
         if (ms) ms[i] = ctx->prof_ms[i];
         if (launches) launches[i] = ctx->prof_launches[i];

@@ -32,11 +32,22 @@ struct jsvd_ctx {
 
     // instrumentation (jsvd_profile)
     bool profiling = false;
-    double prof_ms[4] = {0, 0, 0, 0};
-    long long prof_launches[4] = {0, 0, 0, 0};
-    double prof_flops[4] = {0, 0, 0, 0};
-    std::vector<cudaEvent_t> events;  // 4 per p-step of one sweep
+    static constexpr int kClasses = 5;   // Gram, Jacobi, update (main stream), V update (side stream), other
+    double prof_ms[kClasses] = {0, 0, 0, 0, 0};
+    long long prof_launches[kClasses] = {0, 0, 0, 0, 0};
+    double prof_flops[kClasses] = {0, 0, 0, 0, 0};
+    std::vector<cudaEvent_t> events;  // 6 per p-step of one sweep
     int ensure_events(size_t count);
+
+    // The V update of a p-step runs on a side stream; V' lives in a ring of
+    // kVRing slots guarded by events (no device-side waits).
+    static constexpr int kVRing = 4;
+    bool side_streams = true;
+    cudaStream_t vstream = nullptr;        // least priority: V updates
+    cudaStream_t mstream = nullptr;        // greatest priority: everything else of a solve
+    std::vector<cudaEvent_t> ring_events;  // [0, ring): Jacobi done, [ring, 2 ring): V update done,
+                                           // [2 ring]: join, [2 ring + 1]: fork/join with the caller
+    int ensure_side_stream();
 
     virtual ~jsvd_ctx();
     void set_error(const char *where, cudaError_t e);
@@ -53,6 +64,8 @@ struct jsvd_ctx {
     int backward(int batch, const int *m, const int *n, const double *U, const long long *u_off,
                  const double *S, const long long *s_off, const double *V, const long long *v_off,
                  const double *dU, const double *dS, const double *dV, double *dA, const long long *a_off);
+    int solve_on_stream(int m, int n, int nplus, const double *A, int lda, double *S, double *U, int ldu,
+                        double *V, int ldv, const jsvd_opts *opts, jsvd_info *info, bool hyperbolic);
     int solve(int m, int n, int nplus, const double *A, int lda, double *S, double *U, int ldu,
               double *V, int ldv, const jsvd_opts *opts, jsvd_info *info, bool hyperbolic);
 };

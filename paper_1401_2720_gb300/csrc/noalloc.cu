@@ -34,7 +34,11 @@ struct NoallocCtx : jsvd_ctx {
     size_t used = 0;
     unsigned long long counters_host[8] = {};   // pageable: no cudaMallocHost
 
-    explicit NoallocCtx(void *b) : base(static_cast<unsigned char *>(b)) { host_counters = counters_host; }
+    // one stream, no events: nothing is created
+    explicit NoallocCtx(void *b) : base(static_cast<unsigned char *>(b)) {
+        host_counters = counters_host;
+        side_streams = false;
+    }
 
     int ensure(Buffer &buf, size_t bytes) override {
         if (buf.bytes >= bytes) return 0;

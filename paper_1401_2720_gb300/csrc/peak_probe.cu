@@ -11,28 +11,33 @@
 
 namespace {
 
-constexpr int kChains = 16;   // independent FMA chains per thread
 constexpr int kMma = 8;       // independent mma accumulators per warp
 
-// Each chain has its own multiplier and addend registers, as the operands of
-// a GEMM inner loop do (shared operand registers throttle operand delivery).
+// GEMM-shaped: a 4x4 register tile of accumulators, each FMA depending on the
+// previous one through its addend, the operands taken from two register
+// vectors (as in the update kernel's inner loop, minus its loads).
 __global__ void probe_dfma(double *out, int iters) {
-    double a[kChains], bm[kChains], cm[kChains];
+    double x[4], y[4], acc[4][4];
 #pragma unroll
-    for (int j = 0; j < kChains; ++j) {
-        a[j] = 1e-3 * threadIdx.x + j;
-        bm[j] = 0.9999999 - 1e-9 * j;
-        cm[j] = 1e-7 * (j + 1);
+    for (int i = 0; i < 4; ++i) {
+        x[i] = 1e-3 * threadIdx.x + i;
+        y[i] = 0.5 - 1e-9 * i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
     }
-    for (int i = 0; i < iters; ++i) {
+    for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int j = 0; j < kChains; ++j) a[j] = __fma_rn(a[j], bm[(j + r) % kChains], cm[(j + 3 * r) % kChains]);
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = __fma_rn(x[i], y[(j + r) & 3], acc[i][j]);
     }
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < kChains; ++j) s += a[j];
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s += acc[i][j];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -92,7 +97,7 @@ extern "C" int jsvd_fp64_peak(jsvd_ctx_t ctx, double seconds, double *dfma_tflop
             }
         }
         if (rc) break;
-        const double fl = kind == 0 ? 2.0 * kChains * 8 * (double)iters * blocks * threads
+        const double fl = kind == 0 ? 2.0 * 64 * (double)iters * blocks * threads
                                     : 2.0 * 8 * 8 * 4 * kMma * (double)iters * blocks * (threads / 32);
         const double tf = fl / (ms * 1e-3) / 1e12;
         if (kind == 0 && dfma_tflops) *dfma_tflops = tf;

@@ -48,38 +48,45 @@ __global__ void __launch_bounds__(kUpdThreads) block_update(PStepArgs a, int g_c
 }
 
 template <int BB, typename T>
-static void launch_bb(const PStepArgs &a, cudaStream_t s, cudaEvent_t *ev) {
+static void launch_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
     using C = Cfg<BB>;
-    const size_t sm_gram = gram_smem_bytes<BB, T>();
-    const size_t sm_jac = jacobi_smem_bytes<BB>();
-    const size_t sm_upd = update_smem_bytes<BB, T>();
-    cudaFuncSetAttribute(gram_partial<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gram);
-    cudaFuncSetAttribute(pair_jacobi<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_jac);
-    cudaFuncSetAttribute(block_update<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_upd);
-    if (ev) cudaEventRecord(ev[0], s);
-    gram_partial<BB, T><<<dim3(a.g_chunks, a.npairs), kGramThreads, sm_gram, s>>>(a);
-    if (ev) cudaEventRecord(ev[1], s);
-    pair_jacobi<BB><<<a.npairs, C::kJacThreads, sm_jac, s>>>(a);
-    if (ev) cudaEventRecord(ev[2], s);
-    const int gu = a.g_rows / C::kUpdRows;
-    const int vu = a.V ? a.v_rows / C::kUpdRows : 0;
-    block_update<BB, T><<<dim3(gu + vu, a.npairs), kUpdThreads, sm_upd, s>>>(a, gu);
-    if (ev) cudaEventRecord(ev[3], s);
+    switch (ph) {
+        case Phase::Gram: {
+            const size_t sm = gram_smem_bytes<BB, T>();
+            cudaFuncSetAttribute(gram_partial<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            gram_partial<BB, T><<<dim3(a.g_chunks, a.npairs), kGramThreads, sm, s>>>(a);
+            break;
+        }
+        case Phase::Jacobi: {
+            const size_t sm = jacobi_smem_bytes<BB>();
+            cudaFuncSetAttribute(pair_jacobi<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            pair_jacobi<BB><<<a.npairs, C::kJacThreads, sm, s>>>(a);
+            break;
+        }
+        default: {
+            const size_t sm = update_smem_bytes<BB, T>();
+            cudaFuncSetAttribute(block_update<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            const int gu = (ph == Phase::UpdateV) ? 0 : a.g_rows / C::kUpdRows;
+            const int vu = (ph == Phase::UpdateG || !a.V) ? 0 : a.v_rows / C::kUpdRows;
+            if (gu + vu > 0) block_update<BB, T><<<dim3(gu + vu, a.npairs), kUpdThreads, sm, s>>>(a, gu);
+            break;
+        }
+    }
 }
 
-void launch_pstep_fp64(int BB, const PStepArgs &a, cudaStream_t s, cudaEvent_t *ev) {
+void launch_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s) {
     if (a.fp32) {
         switch (BB) {
-            case 16: launch_bb<16, float>(a, s, ev); break;
-            case 32: launch_bb<32, float>(a, s, ev); break;
-            case 64: launch_bb<64, float>(a, s, ev); break;
+            case 16: launch_bb<16, float>(ph, a, s); break;
+            case 32: launch_bb<32, float>(ph, a, s); break;
+            case 64: launch_bb<64, float>(ph, a, s); break;
             default: break;
         }
     } else {
         switch (BB) {
-            case 16: launch_bb<16, double>(a, s, ev); break;
-            case 32: launch_bb<32, double>(a, s, ev); break;
-            case 64: launch_bb<64, double>(a, s, ev); break;
+            case 16: launch_bb<16, double>(ph, a, s); break;
+            case 32: launch_bb<32, double>(ph, a, s); break;
+            case 64: launch_bb<64, double>(ph, a, s); break;
             default: break;
         }
     }

@@ -52,9 +52,9 @@ struct PStepArgs {
 
 constexpr int kRowAlign = 256;     // g_rows, v_rows are multiples of this
 
-// Launches the three kernels of one p-step on stream s.  If ev is not null,
-// ev[0..3] are recorded before the Gram, Jacobi and update launches and
-// after the update launch.
-void launch_pstep_fp64(int BB, const PStepArgs &a, cudaStream_t s, cudaEvent_t *ev);
+// One kernel of a p-step on stream s: the Gram partials, the per-pair
+// Cholesky + inner sweep, or the update of G, of V, or of both.
+enum class Phase { Gram, Jacobi, UpdateG, UpdateV, UpdateGV };
+void launch_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
 
 }  // namespace jsvd

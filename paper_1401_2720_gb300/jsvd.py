@@ -213,7 +213,7 @@ def rotation_params(hpp: torch.Tensor, hqq: torch.Tensor, hpq: torch.Tensor, hyp
     return cs, tn, pr.bool()
 
 
-KERNEL_CLASSES = ("gram", "jacobi", "update", "other")
+KERNEL_CLASSES = ("gram", "jacobi", "update", "update_v", "other")
 
 
 def profile(enable: bool = True, device: int | None = None) -> None:
@@ -223,11 +223,12 @@ def profile(enable: bool = True, device: int | None = None) -> None:
 
 def profile_read(device: int | None = None) -> dict:
     """{class: (milliseconds, launches, algorithmic flops)} since profile()."""
-    ms = np.zeros(4)
-    ln = np.zeros(4, dtype=np.int64)
-    fl = np.zeros(4)
+    k = len(KERNEL_CLASSES)
+    ms = np.zeros(k)
+    ln = np.zeros(k, dtype=np.int64)
+    fl = np.zeros(k)
     library().jsvd_profile_read(context(device), ms.ctypes.data_as(ctypes.c_void_p),
-                                ln.ctypes.data_as(ctypes.c_void_p), fl.ctypes.data_as(ctypes.c_void_p), 4)
+                                ln.ctypes.data_as(ctypes.c_void_p), fl.ctypes.data_as(ctypes.c_void_p), k)
     return {c: (float(ms[i]), int(ln[i]), float(fl[i])) for i, c in enumerate(KERNEL_CLASSES)}
 
 
