@@ -194,7 +194,17 @@ def run_batched(args) -> None:
     mats, sig, ws, Cs = inputs.workload_batch(args.batch, seed=args.seed)
     pk = J.Packing([a.shape[0] for a in mats], [a.shape[1] for a in mats])
     A = pk.pack(mats, dev)
-    b = args.b if args.b in (8, 16, 32) else None
+    tuned = None
+    if args.b in (8, 16, 32):
+        b = args.b
+    else:
+        # autotuned block width per bucket of n, outside the timed region
+        from paper_1401_2720_gb300 import autotune
+
+        t0 = time.perf_counter()
+        tuned = autotune.tune(mats)
+        tune_s = time.perf_counter() - t0
+        b = autotune.block_widths(pk.n, tuned)
     U, S, V, infos, rc = J.svd_batched_packed(pk, A, b=b, return_info=True, max_sweeps=args.max_sweeps)
     Us, Vs = pk.unpack_mn(U), pk.unpack_nn(V)
     dU = torch.cat([torch.from_numpy(C).to(dev).mm(v).t().reshape(-1) for C, v in zip(Cs, Vs)])
@@ -234,7 +244,9 @@ def run_batched(args) -> None:
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"batch of {len(pk)} matrices, m~U{{16..512}}, n~U{{8..m}}, s log-uniform "
                                f"[1e-6,1] with gaps >= 1e-3, Haar U,V; forward + adjoint backward",
-                   "b": "per-matrix default (8 for n<=256, else 16)" if b is None else b},
+                   "b": (args.b if tuned is None else
+                         {f"n in {autotune.BUCKETS[k]}": v for k, v in sorted(tuned.items())}),
+                   "autotune_s": None if tuned is None else tune_s},
         "matrices_per_s": len(pk) / (ms_step / 1e3),
         "forward_ms": fwd, "backward_ms": bwd, "tflops": flops / (ms_step * 1e-3) / 1e12,
         "sweeps_max": max(i["sweeps"] for i in infos), "sweeps_mean": statistics.mean(i["sweeps"] for i in infos),
@@ -453,7 +465,8 @@ def main():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="graded8192", choices=sorted(WORKLOADS) + ["batched4096"])
     p.add_argument("--batch", type=int, default=4096)
-    p.add_argument("--b", type=int, default=32)
+    p.add_argument("--b", type=int, default=None,
+                   help="block width (default 32; the batched workload autotunes it per bucket of n)")
     p.add_argument("--strategy", default="rR")
     p.add_argument("--max-sweeps", type=int, default=30)
     p.add_argument("--seed", type=int, default=0)
@@ -466,6 +479,8 @@ def main():
     p.add_argument("--cpu-sweeps", type=float, default=12.0,
                    help="sweep count the reference arm scales its sample by")
     args = p.parse_args()
+    if args.b is None and args.workload != "batched4096":
+        args.b = 32
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched4096":

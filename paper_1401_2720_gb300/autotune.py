@@ -1,0 +1,77 @@
+"""Block-width autotuner for the batched solver.
+
+The block width b trades the work of the inner Jacobi sweep (grows with b)
+and the number of p-steps and launches per sweep (shrinks with b) against the
+number of block sweeps the method needs, which depends on the matrices.  Per
+bucket of column counts n, `tune` times one batched solve of a sample of the
+bucket's matrices for each candidate b and keeps the fastest.  The table is
+kept per device name for the life of the process (and in a JSON file when
+`path` is given).
+"""
+
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import jsvd as J
+
+BUCKETS = ((1, 32), (33, 64), (65, 128), (129, 256), (257, 512), (513, 1024))
+_cache: dict[str, dict[int, int]] = {}
+
+
+def bucket_of(n: int) -> int:
+    for k, (lo, hi) in enumerate(BUCKETS):
+        if lo <= n <= hi:
+            return k
+    raise ValueError(f"n = {n} is outside the tuned range")
+
+
+def _time_batch(mats, b: int, device, repeats: int) -> float:
+    pk = J.Packing([a.shape[0] for a in mats], [a.shape[1] for a in mats])
+    A = pk.pack(mats, device)
+    J.svd_batched_packed(pk, A, b=b)                      # warm-up (also builds the tables)
+    torch.cuda.synchronize(device)
+    best = float("inf")
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        J.svd_batched_packed(pk, A, b=b)
+        torch.cuda.synchronize(device)
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def tune(mats, candidates=(8, 16, 32), sample: int = 64, repeats: int = 2, seed: int = 0,
+         path: str | None = None, device=None) -> dict[int, int]:
+    """{bucket index: fastest b} for the buckets that `mats` populate."""
+    device = torch.device(device or "cuda")
+    name = torch.cuda.get_device_name(device)
+    table = dict(_cache.get(name, {}))
+    if path and os.path.exists(path):
+        table.update({int(k): v for k, v in json.load(open(path)).get(name, {}).items()})
+    rng = np.random.default_rng(seed)
+    by_bucket: dict[int, list] = {}
+    for a in mats:
+        by_bucket.setdefault(bucket_of(a.shape[1]), []).append(a)
+    for k, group in sorted(by_bucket.items()):
+        if k in table:
+            continue
+        pick = [group[i] for i in rng.choice(len(group), size=min(sample, len(group)), replace=False)]
+        times = {b: _time_batch(pick, b, device, repeats) for b in candidates}
+        table[k] = min(times, key=times.get)
+    _cache[name] = table
+    if path:
+        data = json.load(open(path)) if os.path.exists(path) else {}
+        data[name] = {str(k): v for k, v in table.items()}
+        with open(path, "w") as f:
+            json.dump(data, f, indent=1)
+    return table
+
+
+def block_widths(ns, table: dict[int, int], default: int = 8) -> np.ndarray:
+    """Per-matrix b from a tuned table (default for untuned buckets)."""
+    return np.array([table.get(bucket_of(int(n)), default) for n in ns], dtype=np.int32)

@@ -31,6 +31,7 @@ using namespace jsvd;
 namespace {
 
 constexpr int kRowPad = 8;        // rows of G and V are padded to multiples of 8
+constexpr int kRing = 4;          // V' slots: the V update of step s may lag the main branch by 3 steps
 constexpr int kMaxSortCols = 1024;
 
 struct BMat {
@@ -80,7 +81,7 @@ struct BArgs {
 };
 
 template <int BB>
-__global__ void __launch_bounds__(kGramThreads) kb_gram(BArgs a, int off, int count, int step) {
+__global__ void __launch_bounds__(Cfg<BB>::kGramThreads) kb_gram(BArgs a, int off, int count, int step) {
     extern __shared__ __align__(16) double smem[];
     const BUnit u = a.units[off + find_unit(a.units + off, count, blockIdx.x)];
     const BMat M = a.mats[u.mat];
@@ -109,25 +110,26 @@ __global__ void __launch_bounds__(Cfg<BB>::kJacThreads) kb_jacobi(BArgs a, int o
                     a.vflag + M.vflag_off + pair, a.counters + (size_t)u.mat * kCntSize, smem);
 }
 
+// which = 0: rows of G, which = 1: rows of V
 template <int BB>
-__global__ void __launch_bounds__(kUpdThreads) kb_update(BArgs a, int off, int count, int step) {
+__global__ void __launch_bounds__(kUpdThreads) kb_update(BArgs a, int off, int count, int step, int which) {
     constexpr int RU = Cfg<BB>::kUpdRows;
     extern __shared__ __align__(16) double smem[];
     const BUnit u = a.units[off + find_unit(a.units + off, count, blockIdx.x)];
     const BMat M = a.mats[u.mat];
     if (!a.stats[u.mat].active) return;
     const int local = blockIdx.x - u.start;
-    const int per = M.ug + M.uv;
+    const int per = which ? M.uv : M.ug;
     const int pair = local / per, c = local % per;
     if (!a.vflag[M.vflag_off + pair]) return;
     const int P = a.tables[M.tab_off + 2 * (step * M.npairs + pair)];
     const int Q = a.tables[M.tab_off + 2 * (step * M.npairs + pair) + 1];
     double *X;
     int ld, r0, valid;
-    if (c < M.ug) {
+    if (!which) {
         X = a.G + M.g_off; ld = M.g_rows; r0 = c * RU; valid = min(RU, M.g_rows - r0);
     } else {
-        X = a.V + M.v_off; ld = M.v_rows; r0 = (c - M.ug) * RU; valid = min(RU, M.v_rows - r0);
+        X = a.V + M.v_off; ld = M.v_rows; r0 = c * RU; valid = min(RU, M.v_rows - r0);
     }
     update_unit<BB, double>(X, ld, r0, valid, P, Q, M.b, a.vprime + M.vp_off + (size_t)pair * BB * BB, smem);
 }
@@ -292,6 +294,23 @@ __global__ void kb_finalize(const BMat *mats, int batch, const long long *col_st
     }
 }
 
+// A kernel launch with an explicit scheduling priority (kept by graph capture).
+template <typename... KArgs, typename... Args>
+void launch_prio(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, int prio,
+                 Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Default block width by size when neither the caller nor opts->b sets one.
 int pick_b(int n) { return n <= 256 ? 8 : 16; }
 
@@ -381,13 +400,14 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         for (auto &M : mats)
             if (2 * M.b == BB) max_steps = std::max(max_steps, M.nb - 1);
         for (int s = 0; s < max_steps; ++s) {
-            for (int kind = 0; kind < 3; ++kind) {
+            for (int kind = 0; kind < 4; ++kind) {   // Gram, Jacobi, update of G, update of V
+                if (kind == 3 && !Vo) continue;
                 LaunchList l{(int)units.size(), 0, 0};
                 for (int i = 0; i < batch; ++i) {
                     const BMat &M = mats[i];
                     if (2 * M.b != BB || s >= M.nb - 1) continue;
                     const int cnt = kind == 0 ? M.npairs * M.g_chunks
-                                  : kind == 1 ? M.npairs : M.npairs * (M.ug + (Vo ? M.uv : 0));
+                                  : kind == 1 ? M.npairs : kind == 2 ? M.npairs * M.ug : M.npairs * M.uv;
                     units.push_back(BUnit{i, l.units});
                     l.units += cnt;
                     ++l.count;
@@ -396,13 +416,11 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
             }
         }
     }
-    if (!Vo)
-        for (auto &M : mats) M.uv = 0;
     // ---- device buffers --------------------------------------------------------
     const size_t need[] = {
         sizeof(BMat) * batch, sizeof(BUnit) * std::max<size_t>(units.size(), 1),
         sizeof(double) * g_tot, sizeof(double) * v_tot, sizeof(double) * std::max<long long>(p_tot, 1),
-        sizeof(double) * std::max<long long>(vp_tot, 1), sizeof(int) * std::max(vf_tot, 1),
+        sizeof(double) * std::max<long long>(vp_tot, 1) * kRing, sizeof(int) * std::max(vf_tot, 1) * kRing,
         sizeof(int) * tables.size(), sizeof(unsigned long long) * kCntSize * batch, sizeof(BStat) * batch,
         sizeof(long long) * batch * 2, sizeof(double) * col_tot, sizeof(int) * col_tot, sizeof(int) * col_tot,
         sizeof(int) * 4};
@@ -456,6 +474,15 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
     // ---- graph: init -> while(sweep) -> finalize ----------------------------------
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return check("stream");
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    cudaStream_t ms[3], vs[3];
+    for (int c = 0; c < 3; ++c) {
+        cudaStreamCreateWithPriority(&ms[c], cudaStreamNonBlocking, prio_greatest);
+        cudaStreamCreateWithPriority(&vs[c], cudaStreamNonBlocking, prio_least);
+    }
+    std::vector<cudaEvent_t> gev(1 + 2 * 3 * kRing + 6);
+    for (auto &e : gev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
     cudaGraph_t graph = nullptr, g_init = nullptr, g_fin = nullptr;
     cudaGraphExec_t exec = nullptr;
     int status = 0;
@@ -487,21 +514,52 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
             cudaSuccess) { fail("capture body"); break; }
+        // One branch per block-width class; inside it the V updates run on a
+        // low-priority branch that trails the main one through a ring of V' slots.
+        cudaEventRecord(gev[0], cs);
+        for (int c = 0; c < 3; ++c) {
+            cudaStreamWaitEvent(ms[c], gev[0], 0);
+            cudaStreamWaitEvent(vs[c], gev[0], 0);
+        }
         for (const Planned &p : plan) {
+            const int c = p.BB == 16 ? 0 : p.BB == 32 ? 1 : 2;
+            const int slot = p.step % kRing;
             BArgs a = ba;
-            a.inner = dinner[p.BB == 16 ? 0 : p.BB == 32 ? 1 : 2];
+            a.inner = dinner[c];
+            a.vprime = ba.vprime + (size_t)slot * vp_tot;
+            a.vflag = ba.vflag + (size_t)slot * vf_tot;
             const int off = p.l.offset, cnt = p.l.count, units_n = p.l.units;
             if (units_n <= 0) continue;
-#define JSVD_LAUNCH_B(BBV)                                                                                     \
-    if (p.BB == BBV) {                                                                                         \
-        if (p.kind == 0) kb_gram<BBV><<<units_n, kGramThreads, gram_smem_bytes<BBV, double>(), cs>>>(a, off, cnt, p.step); \
-        else if (p.kind == 1) kb_jacobi<BBV><<<units_n, Cfg<BBV>::kJacThreads, jacobi_smem_bytes<BBV>(), cs>>>(a, off, cnt, p.step); \
-        else kb_update<BBV><<<units_n, kUpdThreads, update_smem_bytes<BBV, double>(), cs>>>(a, off, cnt, p.step); \
+            cudaEvent_t *jac_done = &gev[1 + (c * kRing + slot) * 2];
+            cudaEvent_t *v_done = jac_done + 1;
+            if (p.kind == 0 && p.step >= kRing && Vo) cudaStreamWaitEvent(ms[c], *v_done, 0);
+            if (p.kind == 3) cudaStreamWaitEvent(vs[c], *jac_done, 0);
+            cudaStream_t st = p.kind == 3 ? vs[c] : ms[c];
+            const int prio = p.kind == 3 ? prio_least : prio_greatest;
+#define JSVD_LAUNCH_B(BBV)                                                                              \
+    if (p.BB == BBV) {                                                                                  \
+        if (p.kind == 0)                                                                                \
+            launch_prio(kb_gram<BBV>, units_n, Cfg<BBV>::kGramThreads, gram_smem_bytes<BBV, double>(), st, \
+                        prio, a, off, cnt, p.step);                                                     \
+        else if (p.kind == 1)                                                                           \
+            launch_prio(kb_jacobi<BBV>, units_n, Cfg<BBV>::kJacThreads, jacobi_smem_bytes<BBV>(), st,   \
+                        prio, a, off, cnt, p.step);                                                     \
+        else                                                                                            \
+            launch_prio(kb_update<BBV>, units_n, kUpdThreads, update_smem_bytes<BBV, double>(), st,     \
+                        prio, a, off, cnt, p.step, p.kind - 2);                                         \
     }
             JSVD_LAUNCH_B(16)
             JSVD_LAUNCH_B(32)
             JSVD_LAUNCH_B(64)
 #undef JSVD_LAUNCH_B
+            if (p.kind == 1) cudaEventRecord(*jac_done, ms[c]);
+            if (p.kind == 3) cudaEventRecord(*v_done, vs[c]);
+        }
+        for (int c = 0; c < 3; ++c) {
+            cudaEventRecord(gev[1 + 2 * 3 * kRing + 2 * c], ms[c]);
+            cudaEventRecord(gev[2 + 2 * 3 * kRing + 2 * c], vs[c]);
+            cudaStreamWaitEvent(cs, gev[1 + 2 * 3 * kRing + 2 * c], 0);
+            cudaStreamWaitEvent(cs, gev[2 + 2 * 3 * kRing + 2 * c], 0);
         }
         kb_sweep_end<<<1, 1024, 0, cs>>>(batch, ba.stats, ba.counters, dmisc, o.max_sweeps, handle);
         if (cudaStreamEndCapture(cs, &body) != cudaSuccess) { fail("capture body end"); break; }
@@ -542,6 +600,11 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
     if (g_init) cudaGraphDestroy(g_init);
     if (g_fin) cudaGraphDestroy(g_fin);
     cudaStreamDestroy(cs);
+    for (int c = 0; c < 3; ++c) {
+        cudaStreamDestroy(ms[c]);
+        cudaStreamDestroy(vs[c]);
+    }
+    for (auto &e : gev) cudaEventDestroy(e);
     if (status) return status;
 
     // ---- statistics ------------------------------------------------------------

@@ -27,7 +27,6 @@ enum {
 };
 
 constexpr int kGramRows = 128;     // rows of [G_P G_Q] per Gram unit
-constexpr int kGramThreads = 256;
 constexpr int kUpdThreads = 256;   // 4x4 output tiles per thread
 
 template <int BB> struct Cfg {
@@ -41,6 +40,11 @@ template <int BB> struct Cfg {
     static constexpr int kPacked = BB * (BB + 1) / 2;
     static constexpr int kUpdRows = 4096 / BB;                        // rows per update unit
     static constexpr int kGramLd = BB + 2;                            // smem row stride
+    // Gram: NBLK 2x2 blocks of the lower triangle; each block's rows are split
+    // over kGramSplit thread groups so that every thread has a block
+    static constexpr int kGramBlocks = (BB / 2) * (BB / 2 + 1) / 2;   // 36, 136, 528
+    static constexpr int kGramSplit = BB == 16 ? 7 : (BB == 32 ? 2 : 1);
+    static constexpr int kGramThreads = BB == 32 ? 288 : 256;
 };
 
 template <typename T> struct Vec2;
@@ -48,7 +52,10 @@ template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 
 template <int BB, typename T>
-constexpr size_t gram_smem_bytes() { return sizeof(T) * kGramRows * Cfg<BB>::kGramLd; }
+constexpr size_t gram_smem_bytes() {
+    return sizeof(T) * kGramRows * Cfg<BB>::kGramLd +
+           (Cfg<BB>::kGramSplit > 1 ? sizeof(T) * 4 * Cfg<BB>::kGramSplit * Cfg<BB>::kGramBlocks : 0);
+}
 template <int BB>
 constexpr size_t jacobi_smem_bytes() { return sizeof(double) * 2 * BB * Cfg<BB>::kLd + (BB - 1) * BB + 16; }
 template <int BB, typename T>
@@ -67,22 +74,27 @@ __device__ __forceinline__ int packed_lower(int i, int j) {
 // ---------------------------------------------------------------------------
 // Gram partial of rows [r0, r0 + valid) (valid <= kGramRows).  The chunk is
 // staged row-major in shared memory (row stride BB+2) so that every thread
-// reads 2x2 operand blocks with vector loads; thread t owns the 2x2 blocks
-// (I, J), I >= J, t, t+256, ... of the lower triangle and sums over the rows
-// in increasing order.  The result (double) goes to out[packed index].
+// reads 2x2 operand blocks with vector loads.  The 2x2 blocks (I, J), I >= J,
+// of the lower triangle are spread over the threads; with kGramSplit > 1 the
+// rows of a block are split over that many thread groups (group g takes rows
+// g, g + split, ...) and the group sums are added in group order.  Each
+// partial sum runs over its rows in increasing order.  The result (double)
+// goes to out[packed index].
 template <int BB, typename T>
 __device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int r0, int valid, int P,
                                           int Q, int b, double *__restrict__ out, T *X) {
     using C = Cfg<BB>;
     using T2 = typename Vec2<T>::type;
-    for (int e = threadIdx.x; e < kGramRows * BB; e += kGramThreads) {
+    constexpr int NBLK = C::kGramBlocks;
+    constexpr int SPLIT = C::kGramSplit;
+    for (int e = threadIdx.x; e < kGramRows * BB; e += C::kGramThreads) {
         const int r = e % kGramRows, j = e / kGramRows;
         if (r < valid) X[r * C::kGramLd + j] = G[(size_t)block_col(P, Q, b, j) * ldg + r0 + r];
     }
     __syncthreads();
-    constexpr int NB = BB / 2;
-    constexpr int NBLK = NB * (NB + 1) / 2;
-    for (int blk = threadIdx.x; blk < NBLK; blk += kGramThreads) {
+    T *red = X + kGramRows * C::kGramLd;   // [SPLIT][NBLK][4] when SPLIT > 1
+    for (int task = threadIdx.x; task < NBLK * SPLIT; task += C::kGramThreads) {
+        const int blk = task % NBLK, grp = task / NBLK;
         int I = (int)((sqrtf(8.0f * blk + 1.0f) - 1.0f) * 0.5f);
         while ((I + 1) * (I + 2) / 2 <= blk) ++I;
         while (I * (I + 1) / 2 > blk) --I;
@@ -90,7 +102,7 @@ __device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int 
         T h00 = 0, h10 = 0, h01 = 0, h11 = 0;
         const T *xi = X + 2 * I, *xj = X + 2 * J;
 #pragma unroll 4
-        for (int r = 0; r < valid; ++r) {
+        for (int r = grp; r < valid; r += SPLIT) {
             const T2 u = *reinterpret_cast<const T2 *>(xi + r * C::kGramLd);
             const T2 v = *reinterpret_cast<const T2 *>(xj + r * C::kGramLd);
             h00 = fma(u.x, v.x, h00);
@@ -98,11 +110,30 @@ __device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int 
             h01 = fma(u.x, v.y, h01);
             h11 = fma(u.y, v.y, h11);
         }
-        const int i0 = 2 * I, j0 = 2 * J;
-        out[packed_lower<BB>(i0, j0)] = (double)h00;
-        out[packed_lower<BB>(i0 + 1, j0)] = (double)h10;
-        out[packed_lower<BB>(i0 + 1, j0 + 1)] = (double)h11;
-        if (I != J) out[packed_lower<BB>(i0, j0 + 1)] = (double)h01;
+        if (SPLIT > 1) {
+            T *dst = red + 4 * (grp * NBLK + blk);
+            dst[0] = h00; dst[1] = h10; dst[2] = h01; dst[3] = h11;
+        } else {
+            const int i0 = 2 * I, j0 = 2 * J;
+            out[packed_lower<BB>(i0, j0)] = (double)h00;
+            out[packed_lower<BB>(i0 + 1, j0)] = (double)h10;
+            out[packed_lower<BB>(i0 + 1, j0 + 1)] = (double)h11;
+            if (I != J) out[packed_lower<BB>(i0, j0 + 1)] = (double)h01;
+        }
+    }
+    if (SPLIT > 1) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < NBLK * 4; t += C::kGramThreads) {
+            const int blk = t / 4, c = t % 4;
+            T acc = red[4 * blk + c];
+            for (int g = 1; g < SPLIT; ++g) acc += red[4 * (g * NBLK + blk) + c];
+            int I = (int)((sqrtf(8.0f * blk + 1.0f) - 1.0f) * 0.5f);
+            while ((I + 1) * (I + 2) / 2 <= blk) ++I;
+            while (I * (I + 1) / 2 > blk) --I;
+            const int J = blk - I * (I + 1) / 2;
+            const int i = 2 * I + (c & 1), j = 2 * J + (c >> 1);
+            if (i >= j) out[packed_lower<BB>(i, j)] = (double)acc;
+        }
     }
 }
 

@@ -8,7 +8,7 @@
 namespace jsvd {
 
 template <int BB, typename T>
-__global__ void __launch_bounds__(kGramThreads) gram_partial(PStepArgs a) {
+__global__ void __launch_bounds__(Cfg<BB>::kGramThreads) gram_partial(PStepArgs a) {
     extern __shared__ __align__(16) double smem[];
     const int pair = blockIdx.y, chunk = blockIdx.x;
     const int P = a.table[2 * (a.step * a.npairs + pair)];
@@ -54,7 +54,7 @@ static void launch_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
         case Phase::Gram: {
             const size_t sm = gram_smem_bytes<BB, T>();
             cudaFuncSetAttribute(gram_partial<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            gram_partial<BB, T><<<dim3(a.g_chunks, a.npairs), kGramThreads, sm, s>>>(a);
+            gram_partial<BB, T><<<dim3(a.g_chunks, a.npairs), C::kGramThreads, sm, s>>>(a);
             break;
         }
         case Phase::Jacobi: {
