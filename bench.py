@@ -260,7 +260,7 @@ def run_gpu(args) -> None:
     import torch
     import torch.distributed as dist
 
-    from paper_1401_2720_gb300 import build_ext
+    from paper_1401_2720_gb300 import build_ext, replicas
     from paper_1401_2720_gb300 import jsvd as J
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -276,7 +276,7 @@ def run_gpu(args) -> None:
         dist.barrier()
 
     m, n, _, desc = WORKLOADS[args.workload]
-    A_host = make_input(args.workload, args.seed + rank)
+    A_host = make_input(args.workload, replicas.rank_seed(args.seed, rank))
     A = torch.from_numpy(np.ascontiguousarray(A_host.T)).to(dev).t()      # column-major view
     U = torch.empty((n, m), dtype=torch.float64, device=dev).t()
     S = torch.empty(n, dtype=torch.float64, device=dev)
@@ -322,12 +322,8 @@ def run_gpu(args) -> None:
     ms_total = e0.elapsed_time(e1)
     prof = J.profile_read()
     J.profile(False)
-    ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = ms_step / 1e3 / world                    # s per matrix, whole job
+    ms_step, matrices = replicas.whole_job(ms_total / args.steps, 1, device=dev)
+    value = replicas.seconds_per_matrix(ms_step, matrices)   # s per matrix, whole job
 
     # ---- e2e: host (pinned) -> device, SVD, results -> host --------------------
     e2e = None
@@ -351,12 +347,9 @@ def run_gpu(args) -> None:
             V_h.copy_(V.t(), non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = f0.elapsed_time(f1) / args.e2e_steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": e2e_ms / 1e3 / world, "unit": "s/matrix", "h2d_bytes_per_step": m * n * 8 * world,
+        e2e_ms, e2e_mats = replicas.whole_job(f0.elapsed_time(f1) / args.e2e_steps, 1, device=dev)
+        e2e = {"value": replicas.seconds_per_matrix(e2e_ms, e2e_mats), "unit": "s/matrix",
+               "h2d_bytes_per_step": m * n * 8 * world,
                "d2h_bytes_per_step": (m * n + n + n * n) * 8 * world}
 
     if rank != 0:
@@ -399,6 +392,7 @@ def run_gpu(args) -> None:
         # plain FP64 run of the same matrix, outside the timed region
         kw64 = dict(kw)
         kw64.pop("precision")
+        kw64["max_sweeps"] = max(args.max_sweeps, 60)   # let the plain FP64 solve converge
         U64 = torch.empty_like(U)
         S64 = torch.empty_like(S)
         V64 = torch.empty_like(V)

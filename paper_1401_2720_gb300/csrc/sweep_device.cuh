@@ -170,14 +170,24 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     for (int e = tid; e < (BB - 1) * BB; e += C::kJacThreads) tab[e] = inner[e];
     if (tid == 0) { s_off = 0ull; s_brk = 0; s_cnt[0] = 0; s_cnt[1] = 0; }
 
-    // (1) H = sum of the row-chunk partials, in chunk order
+    // (1) H = sum of the row-chunk partials in a fixed order: chunk c goes to
+    // accumulator c mod 8 (in increasing c), then the 8 accumulators are added
+    // pairwise; short dependency chains keep the FP64 latency off the path
     for (int e = tid; e < BB * BB; e += C::kJacThreads) {
         const int i = e % BB, j = e / BB;
         if (i < j) continue;
         const int k = packed_lower<BB>(i, j);
-        double s = 0.0;
-        for (int c = 0; c < chunks; ++c) s = __dadd_rn(s, part[(size_t)c * C::kPacked + k]);
-        A[i + j * C::kLd] = s;
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int c = 0;
+        for (; c + 8 <= chunks; c += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = __dadd_rn(acc[u], part[(size_t)(c + u) * C::kPacked + k]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (c + u < chunks) acc[u] = __dadd_rn(acc[u], part[(size_t)(c + u) * C::kPacked + k]);
+        A[i + j * C::kLd] = __dadd_rn(__dadd_rn(__dadd_rn(acc[0], acc[1]), __dadd_rn(acc[2], acc[3])),
+                                      __dadd_rn(__dadd_rn(acc[4], acc[5]), __dadd_rn(acc[6], acc[7])));
     }
     __syncthreads();
 
