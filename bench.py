@@ -461,7 +461,7 @@ def main():
     p.add_argument("--batch", type=int, default=4096)
     p.add_argument("--b", type=int, default=None,
                    help="block width (default 32; the batched workload autotunes it per bucket of n)")
-    p.add_argument("--strategy", default="rR")
+    p.add_argument("--strategy", default=None, help="pivot strategy (default rR; modulus for small512)")
     p.add_argument("--max-sweeps", type=int, default=30)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--e2e-steps", type=int, default=1)
@@ -474,7 +474,12 @@ def main():
                    help="sweep count the reference arm scales its sample by")
     args = p.parse_args()
     if args.b is None and args.workload != "batched4096":
-        args.b = 32
+        # block widths chosen by timing b in {16, 32} on this GPU: 32 for the
+        # graded 8192^2 and mixed workloads, 16 for the 4096^2 HSVD (only 64 pivot
+        # pairs per p-step at b = 32, so its latency-bound Jacobi phase dominates)
+        args.b = 16 if WORKLOADS[args.workload][2] == "hsvd" or args.workload == "small512" else 32
+    if args.strategy is None:
+        args.strategy = "modulus" if args.workload == "small512" else "rR"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched4096":

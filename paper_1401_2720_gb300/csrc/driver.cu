@@ -146,7 +146,7 @@ __global__ void k_rot_params(int count, const double *hpp, const double *hqq, co
                              const int *hyp, double *cs, double *tn, int *proper) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    const Rot r = rot_params(hpp[i], hqq[i], hpq[i], hyp[i] ? -1.0 : 1.0);
+    const Rot r = rot_params(hpp[i], hqq[i], hpq[i], hyp[i] != 0);
     cs[i] = r.cs;
     tn[i] = r.tn;
     proper[i] = r.cs != 1.0;

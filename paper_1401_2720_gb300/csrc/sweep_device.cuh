@@ -191,14 +191,19 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     }
     __syncthreads();
 
-    // (2) normalized off-diagonal maximum of H (convergence report)
+    // (2) normalized off-diagonal maximum of H, max |h_ij| / sqrt(h_ii h_jj)
+    // (reported only): B[j] = 1/sqrt(h_jj) first, then two products per entry
+    for (int j = tid; j < BB; j += C::kJacThreads) {
+        const double d = A[j + j * C::kLd];
+        B[j] = d > 0.0 ? rsqrt(d) : 0.0;
+    }
+    __syncthreads();
     {
         double mx = 0.0;
         for (int e = tid; e < BB * BB; e += C::kJacThreads) {
             const int i = e % BB, j = e / BB;
             if (i <= j) continue;
-            const double d = A[i + i * C::kLd] * A[j + j * C::kLd];
-            if (d > 0.0) mx = fmax(mx, fabs(A[i + j * C::kLd]) / sqrt(d));
+            mx = fmax(mx, fabs(A[i + j * C::kLd]) * B[i] * B[j]);
         }
         atomicMax(&s_off, (unsigned long long)__double_as_longlong(mx));
     }
@@ -270,13 +275,13 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
                 hpq = __dadd_rn(hpq, __shfl_xor_sync(0xffffffffu, hpq, off));
             }
             const int gp = block_col(P, Q, b, p), gq = block_col(P, Q, b, q);
-            const double t = (gp < nplus && gq >= nplus) ? -1.0 : 1.0;
+            const bool hyp = gp < nplus && gq >= nplus;
             const bool border = (gp >= bord_lo && gp < bord_hi) || (gq >= bord_lo && gq < bord_hi);
             const bool rho = !border && needs_rotation(hpp, hqq, hpq, c_eps);
             Rot rot{1.0, 0.0};
-            if (rho) rot = rot_params(hpp, hqq, hpq, t);
+            if (rho) rot = rot_params(hpp, hqq, hpq, hyp);
             bool swap = false;
-            if (t > 0.0 && !border) {
+            if (!hyp && !border) {
                 const double npp = rho ? __fma_rn(-rot.tn, hpq, hpp) : hpp;
                 const double nqq = rho ? __fma_rn(rot.tn, hpq, hqq) : hqq;
                 swap = (gq < nplus && npp < nqq) || (gp >= nplus && npp > nqq);
@@ -287,7 +292,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
                     const int r = g + k * C::kLanesPerPair;
                     double x = rp[r], z = rq[r];
                     double u = wp[r], v = wq[r];
-                    if (rho) { rot_apply(x, z, t, rot); rot_apply(u, v, t, rot); }
+                    if (rho) { rot_apply(x, z, hyp, rot); rot_apply(u, v, hyp, rot); }
                     if (swap) {
                         rp[r] = z; rq[r] = x; wp[r] = v; wq[r] = u;
                     } else {
@@ -299,7 +304,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
             if (g == 0 && rho) {
                 ++my_rot;
                 ++sweep_rot;
-                if (rot.cs != 1.0) ++my_proper;
+                if (is_proper(rot)) ++my_proper;
             }
             __syncthreads();
         }
