@@ -47,25 +47,38 @@ __global__ void __launch_bounds__(kUpdThreads) block_update(PStepArgs a, int g_c
     update_unit<BB, T>(M, ld, r0, RU, P, Q, a.b, a.vprime + (size_t)pair * BB * BB, reinterpret_cast<T *>(smem));
 }
 
+// The dynamic shared memory limit of each kernel is raised once per device.
+template <int BB, typename T>
+static void configure_once() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(gram_partial<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)gram_smem_bytes<BB, T>());
+    cudaFuncSetAttribute(pair_jacobi<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem_bytes<BB>());
+    cudaFuncSetAttribute(block_update<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)update_smem_bytes<BB, T>());
+    done[dev] = true;
+}
+
 template <int BB, typename T>
 static void launch_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
     using C = Cfg<BB>;
+    configure_once<BB, T>();
     switch (ph) {
         case Phase::Gram: {
             const size_t sm = gram_smem_bytes<BB, T>();
-            cudaFuncSetAttribute(gram_partial<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             gram_partial<BB, T><<<dim3(a.g_chunks, a.npairs), C::kGramThreads, sm, s>>>(a);
             break;
         }
         case Phase::Jacobi: {
             const size_t sm = jacobi_smem_bytes<BB>();
-            cudaFuncSetAttribute(pair_jacobi<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             pair_jacobi<BB><<<a.npairs, C::kJacThreads, sm, s>>>(a);
             break;
         }
         default: {
             const size_t sm = update_smem_bytes<BB, T>();
-            cudaFuncSetAttribute(block_update<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             const int gu = (ph == Phase::UpdateV) ? 0 : a.g_rows / C::kUpdRows;
             const int vu = (ph == Phase::UpdateG || !a.V) ? 0 : a.v_rows / C::kUpdRows;
             if (gu + vu > 0) block_update<BB, T><<<dim3(gu + vu, a.npairs), kUpdThreads, sm, s>>>(a, gu);

@@ -129,3 +129,15 @@ def test_batched_autograd_matches_direct(cuda):
         un, sn, vn = _np(u), _np(s), _np(v)
         ref = O.svd_adjoint(un, sn, vn, C @ vn, w, C.T @ un)
         assert np.linalg.norm(_np(x.grad) - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("strategy", ["modulus", "R", "C", "rC"])
+def test_batched_other_orderings(cuda, strategy):
+    mats, sig, _, _ = _batch(10, seed=30, m_hi=120)
+    pk = J.Packing([a.shape[0] for a in mats], [a.shape[1] for a in mats])
+    U, S, V, infos, rc = J.svd_batched_packed(pk, pk.pack(mats, cuda), b=8, strategy=strategy,
+                                              return_info=True)
+    assert rc == 0
+    for a, s_true, s, v in zip(mats, sig, pk.unpack_n(S), pk.unpack_nn(V)):
+        assert np.max(np.abs(_np(s) - s_true)) / s_true[0] <= 1e-12
+        assert _orth(_np(v)) <= 50 * max(a.shape[1], 2) * EPS

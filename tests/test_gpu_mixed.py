@@ -55,3 +55,11 @@ def test_mixed_hsvd(cuda):
     assert info["converged"]
     _, So, _, _ = O.hsvd(G, 64)
     assert np.max(np.abs(_np(S) - So)) / So.max() <= 1e-12
+
+
+def test_mixed_bordered_shape(cuda):
+    A, s_true = I.workload_mixed(210, 83, seed=9)
+    U, S, V, info = J.svd(_t(A, cuda), b=16, precision="mixed", return_info=True)
+    assert info["converged"]
+    assert np.max(np.abs(_np(S) - s_true)) <= 1e-12 * s_true[0]
+    assert _orth(_np(V)) <= 50 * 83 * EPS

@@ -189,3 +189,21 @@ def test_zero_matrix(cuda):
     U, S, V = J.svd(_t(A, cuda), b=8)
     assert torch.all(S == 0) and torch.all(U == 0)
     assert _orth(_np(V)) == 0.0
+
+
+@pytest.mark.parametrize("mn_plus", [(150, 100, 37), (90, 61, 0), (70, 45, 45), (64, 33, 1)])
+def test_hsvd_bordered(cuda, mn_plus):
+    """HSVD with n not a multiple of 2b: the border goes in at the J boundary."""
+    m, n, npl = mn_plus
+    rng = np.random.default_rng(m + n + npl)
+    G = np.asfortranarray(rng.standard_normal((m, n)))
+    U, S, V, info = J.hsvd(_t(G, cuda), npl, b=8, return_info=True)
+    assert info["converged"]
+    _, So, _, _ = O.hsvd(G, npl, strategy="modulus")
+    S, U, V = _np(S), _np(U), _np(V)
+    assert np.max(np.abs(S - So)) / So.max() <= 1e-12
+    j = np.where(np.arange(n) < npl, 1.0, -1.0)
+    Jm = np.diag(j)
+    nv = np.linalg.norm(V, 2) ** 2
+    assert np.abs(V.T @ Jm @ V - Jm).max() <= 50 * n * EPS * nv
+    assert np.linalg.norm(G - (U * S) @ V.T) <= 50 * n * EPS * np.linalg.norm(G) * nv
