@@ -130,7 +130,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_sample(A: np.ndarray, b: int, strategy: str, pairs: int, sweeps_hint: float, nplus: int | None = None):
+def variant_name(inner_sweeps: int) -> str:
+    if inner_sweeps <= 1:
+        return "block-oriented (one inner sweep)"
+    return f"full block (at most {inner_sweeps} inner sweeps)"
+
+
+def cpu_sample(A: np.ndarray, b: int, strategy: str, pairs: int, sweeps_hint: float, nplus: int | None = None,
+               inner_sweeps: int = 1):
     """Time the oracle's block-oriented p-step on `pairs` pivot pairs of the
     full-size input and scale to s/matrix: (t / pairs) x pairs per sweep x sweeps."""
     import oracle
@@ -143,12 +150,12 @@ def cpu_sample(A: np.ndarray, b: int, strategy: str, pairs: int, sweeps_hint: fl
     V = np.asfortranarray(np.eye(n))
     step = tab[0][:pairs]
     t0 = time.perf_counter()
-    oracle.block_pstep(G, V, b, step, inner, nplus=nplus)
+    oracle.block_pstep(G, V, b, step, inner, nplus=nplus, inner_sweeps=inner_sweeps)
     t = time.perf_counter() - t0
     per_pair = t / len(step)
     pairs_per_sweep = (nb // 2) * (nb - 1)
     est = per_pair * pairs_per_sweep * sweeps_hint
-    sample = (f"{len(step)} pivot pairs of p-step 1 of the oracle's block-oriented method (b={b}) on the "
+    sample = (f"{len(step)} pivot pairs of p-step 1 of the oracle's {variant_name(inner_sweeps)} method (b={b}) on the "
               f"full {m}x{n} input, {t:.2f} s, scaled by {pairs_per_sweep} pairs/sweep x {sweeps_hint:g} sweeps")
     return est, sample
 
@@ -162,7 +169,7 @@ def run_reference(args) -> None:
     sample = ""
     for i in range(args.warmup + args.steps):
         nplus = A.shape[1] // 2 if WORKLOADS[args.workload][2] == "hsvd" else None
-        v, sample = cpu_sample(A, args.b, args.strategy, args.cpu_pairs, args.cpu_sweeps, nplus)
+        v, sample = cpu_sample(A, args.b, args.strategy, args.cpu_pairs, args.cpu_sweeps, nplus, args.inner_sweeps)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
@@ -172,7 +179,8 @@ def run_reference(args) -> None:
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "b": args.b, "strategy": args.strategy},
+        "config": {"workload": desc, "b": args.b, "strategy": args.strategy,
+                   "variant": variant_name(args.inner_sweeps)},
         "cpu_baseline": {"value": value, "unit": "s/matrix", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "s/matrix", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -282,7 +290,7 @@ def run_gpu(args) -> None:
     S = torch.empty(n, dtype=torch.float64, device=dev)
     V = torch.empty((n, n), dtype=torch.float64, device=dev).t()
     kind = WORKLOADS[args.workload][2]
-    kw = dict(b=args.b, strategy=args.strategy, max_sweeps=args.max_sweeps)
+    kw = dict(b=args.b, strategy=args.strategy, max_sweeps=args.max_sweeps, inner_sweeps=args.inner_sweeps)
     if kind == "mixed":
         kw["precision"] = "mixed"
 
@@ -426,7 +434,7 @@ def run_gpu(args) -> None:
         if mixed_report:
             sweeps = mixed_report["plain_sweeps"]
         est, sample = cpu_sample(A_host, args.b if args.b else infos[-1]["b"], args.strategy,
-                                 args.cpu_pairs, sweeps, n // 2 if kind == "hsvd" else None)
+                                 args.cpu_pairs, sweeps, n // 2 if kind == "hsvd" else None, args.inner_sweeps)
         cpu = {"value": est, "unit": "s/matrix", "cores": 1, "kind": "oracle", "sample": sample}
 
     last = infos[-1]
@@ -435,7 +443,7 @@ def run_gpu(args) -> None:
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "seed": args.seed, "b": last["b"], "strategy": args.strategy,
-                   "variant": "block-oriented (one inner sweep)", "l2": "inputs larger than L2 (no flush)",
+                   "variant": variant_name(args.inner_sweeps), "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "tflops": flops_total / (ms_total * 1e-3) / 1e12 if ms_total else None,
         "sweeps": [i["sweeps"] for i in infos], "converged": all(i["converged"] for i in infos),
@@ -463,6 +471,8 @@ def main():
                    help="block width (default 32; the batched workload autotunes it per bucket of n)")
     p.add_argument("--strategy", default=None, help="pivot strategy (default rR; modulus for small512)")
     p.add_argument("--max-sweeps", type=int, default=30)
+    p.add_argument("--inner-sweeps", type=int, default=1,
+                   help="inner sweeps per pivot pair: 1 = block-oriented, 30 = full block (Sec. 4.3)")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")

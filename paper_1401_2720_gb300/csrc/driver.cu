@@ -435,7 +435,9 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
 
     const double bbd = (double)BB;
     const double fl_gram = (double)npairs * m * bbd * (bbd + 1.0);
-    const double fl_jac = (double)npairs * (9.0 * bbd * bbd * (bbd - 1.0) + bbd * bbd * bbd / 3.0);
+    // Cholesky once per pair, then 9 bb^2 (bb - 1) per inner sweep performed
+    const double fl_chol = bbd * bbd * bbd / 3.0;
+    const double fl_inner = 9.0 * bbd * bbd * (bbd - 1.0);
     const double fl_upd_g_pair = 2.0 * (double)m * bbd * bbd;
     const double fl_upd_v_pair = want_v ? 2.0 * (double)n * bbd * bbd : 0.0;
 
@@ -491,7 +493,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
             if (int r = sync("sweep")) return r;
             ++*done;
             prof_flops[0] += fl_gram * (nb - 1);
-            prof_flops[1] += fl_jac * (nb - 1);
+            prof_flops[1] += fl_chol * (double)npairs * (nb - 1) + fl_inner * (double)host_counters[kCntInner];
             if (side) {
                 prof_flops[2] += fl_upd_g_pair * (double)host_counters[kCntUpdated];
                 prof_flops[3] += fl_upd_v_pair * (double)host_counters[kCntUpdated];

@@ -23,6 +23,7 @@ enum {
     kCntBreak = 3,     // Cholesky breakdowns
     kCntOff = 4,       // max normalized off-diagonal |h_ij|/sqrt(h_ii h_jj), double bits
     kCntErr = 5,       // device-side error flags
+    kCntInner = 6,     // inner sweeps performed, summed over the pivot pairs
     kCntSize = 8
 };
 
@@ -251,9 +252,10 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     const int y = tid / C::kLanesPerPair;
     const int g = tid % C::kLanesPerPair;
     const double c_eps = eps * sqrt((double)BB);   // c(eps) = eps sqrt(nhat), nhat = BB
-    int my_rot = 0, my_proper = 0, changed = 0;
+    int my_rot = 0, my_proper = 0, changed = 0, sweeps_done = 0;
     for (int sw = 0; sw < inner_sweeps; ++sw) {
         int sweep_rot = 0;
+        ++sweeps_done;
         for (int st = 0; st < BB - 1; ++st) {
             const int p = tab[2 * (st * (BB / 2) + y)];
             const int q = tab[2 * (st * (BB / 2) + y) + 1];
@@ -325,6 +327,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
         atomicAdd(&counters[kCntRot], (unsigned long long)s_cnt[0]);
         atomicAdd(&counters[kCntProper], (unsigned long long)s_cnt[1]);
         if (any_change) atomicAdd(&counters[kCntUpdated], 1ull);
+        atomicAdd(&counters[kCntInner], (unsigned long long)sweeps_done);
         if (s_brk) atomicAdd(&counters[kCntBreak], (unsigned long long)s_brk);
         atomicMax(&counters[kCntOff], s_off);
     }
