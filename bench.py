@@ -290,7 +290,8 @@ def run_gpu(args) -> None:
     S = torch.empty(n, dtype=torch.float64, device=dev)
     V = torch.empty((n, n), dtype=torch.float64, device=dev).t()
     kind = WORKLOADS[args.workload][2]
-    kw = dict(b=args.b, strategy=args.strategy, max_sweeps=args.max_sweeps, inner_sweeps=args.inner_sweeps)
+    kw = dict(b=args.b, strategy=args.strategy, max_sweeps=args.max_sweeps, inner_sweeps=args.inner_sweeps,
+              contraction=args.contraction)
     if kind == "mixed":
         kw["precision"] = "mixed"
 
@@ -471,6 +472,8 @@ def main():
                    help="block width (default 32; the batched workload autotunes it per bucket of n)")
     p.add_argument("--strategy", default=None, help="pivot strategy (default rR; modulus for small512)")
     p.add_argument("--max-sweeps", type=int, default=30)
+    p.add_argument("--contraction", default="fp64", choices=["fp64", "split"],
+                   help="FP64 block contractions: FP64 FMA kernels or split bf16 digits on the tensor cores")
     p.add_argument("--inner-sweeps", type=int, default=1,
                    help="inner sweeps per pivot pair: 1 = block-oriented, 30 = full block (Sec. 4.3)")
     p.add_argument("--seed", type=int, default=0)

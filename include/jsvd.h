@@ -52,6 +52,17 @@ extern "C" {
 #define JSVD_PREC_FP64       0  /* all sweeps in FP64 */
 #define JSVD_PREC_MIXED      1  /* FP32 block sweeps, then FP64 sweeps to convergence */
 
+/* ---- how the FP64 block contractions are evaluated ----------------------
+ * The Gram matrix of a pivot pair (Eq. (2.7)) and the block update (Eq. (2.9))
+ * of the FP64 sweeps.  The paper forms both with FP64 arithmetic.  SPLIT forms
+ * them on the bf16 tensor cores from exact 7-bit digit slices of power-of-two
+ * scaled fixed-point operands (9 slices, 45 digit products per FP64 product,
+ * exact FP32 accumulation, one FP64 rounding per result); with the column
+ * scaling it applies its error is at or below that of the FP64 FMA form.
+ * Used by jsvd_dgesvj, jsvd_dhsvj and the FP64 stage of the mixed solver. */
+#define JSVD_CONTRACT_FP64   0  /* FP64 FMA kernels */
+#define JSVD_CONTRACT_SPLIT  1  /* split bf16 digits on the tensor cores */
+
 typedef struct jsvd_ctx *jsvd_ctx_t;
 
 typedef struct {
@@ -63,6 +74,7 @@ typedef struct {
     int max_sweeps;      /* limit on block sweeps (0: 30) */
     int precision;       /* JSVD_PREC_* */
     int sort;            /* 1: sigma non-increasing (per sign block for the HSVD) */
+    int contraction;     /* JSVD_CONTRACT_*; the batched solver always uses FP64 */
 } jsvd_opts;
 
 typedef struct {

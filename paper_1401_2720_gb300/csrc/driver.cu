@@ -228,7 +228,8 @@ int jsvd_ctx::inner_table(int strategy, int BB, const unsigned char **dev) {
 }
 
 jsvd_ctx::~jsvd_ctx() {
-    for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &g32, &v32,
+    for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp,
+                      &g32, &v32,
                       &tmp_a, &tmp_b, &tmp_g, &b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag,
                       &b_tab, &b_cnt, &b_stat, &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &adj_w,
                       &adj_meta, &adj_desc})
@@ -322,6 +323,15 @@ int choose_b(const jsvd_opts &o, int n) {
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Elements of one pair's split right factor (one version) for pivot order BB.
+size_t split_b_elems_rt(int BB) {
+    switch (BB) {
+        case 16: return split_b_elems<16>();
+        case 32: return split_b_elems<32>();
+        default: return split_b_elems<64>();
+    }
+}
+
 }  // namespace
 
 // The solve runs on a high-priority stream of the library (the V updates on a
@@ -358,6 +368,10 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         last_error = "unknown precision mode";
         return JSVD_ERR_UNSUPPORTED;
     }
+    if (o.contraction != JSVD_CONTRACT_FP64 && o.contraction != JSVD_CONTRACT_SPLIT) {
+        last_error = "unknown contraction mode";
+        return JSVD_ERR_UNSUPPORTED;
+    }
     const int b = choose_b(o, n);
     if (b != 8 && b != 16 && b != 32) {
         last_error = "block width must be 8, 16 or 32";
@@ -386,6 +400,13 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
     const int ring = side_streams ? kVRing : 1;
     if ((rc = ensure(vprime, sizeof(double) * (size_t)npairs * BB * BB * ring))) return rc;
     if ((rc = ensure(vflag, sizeof(int) * (size_t)npairs * ring))) return rc;
+    const bool split = o.contraction == JSVD_CONTRACT_SPLIT;
+    const size_t bsl_pairs = (size_t)npairs * 2 * (size_t)split_b_elems_rt(BB);   // per ring slot
+    if (split) {
+        if ((rc = ensure(bslice, sizeof(uint16_t) * bsl_pairs * ring))) return rc;
+        if ((rc = ensure(bexp, sizeof(int) * (size_t)npairs * 2 * BB * ring))) return rc;
+        if ((rc = ensure(dexp, sizeof(int) * (size_t)npairs * BB * ring))) return rc;
+    }
     if (side_streams && (rc = ensure_side_stream())) return rc;
     if ((rc = ensure(counters, sizeof(unsigned long long) * kCntSize))) return rc;
     if ((rc = ensure(sigma, sizeof(double) * (size_t)n_pad))) return rc;
@@ -457,6 +478,11 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
                 a.step = s;
                 a.vprime = (double *)vprime.ptr + (size_t)slot * npairs * BB * BB;
                 a.vflag = (int *)vflag.ptr + (size_t)slot * npairs;
+                if (a.split) {
+                    a.bslice = (uint16_t *)bslice.ptr + (size_t)slot * bsl_pairs;
+                    a.bexp = (int *)bexp.ptr + (size_t)slot * npairs * 2 * BB;
+                    a.dexp = (int *)dexp.ptr + (size_t)slot * npairs * BB;
+                }
                 cudaEvent_t *ev = profiling ? &events[6 * (size_t)s] : nullptr;
                 if (side && s >= ring) cudaStreamWaitEvent(stream, ring_events[ring + slot], 0);
                 if (ev) cudaEventRecord(ev[0], stream);
@@ -540,14 +566,14 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         k_to_f32<<<1024, 256, 0, stream>>>(G, G32, (size_t)g_rows * n_pad);
         k_eye_f32<<<1024, 256, 0, stream>>>(V32, v_rows, v_rows, n_pad);
         prof_launches[4] += 2;
-        a.G = G32; a.V = V32; a.fp32 = 1; a.eps = 0x1p-24;
+        a.G = G32; a.V = V32; a.fp32 = 1; a.eps = 0x1p-24; a.split = 0;
         int low_done = 0, low_conv = 0;
         if ((rc = sweep_loop(o.max_sweeps, &low_done, &low_conv))) return rc;
         inf.sweeps_low = low_done;
         // Stage 2: Q = polar factor of V32 in FP64, G := G Q, V := Q.
         if ((rc = polar_and_apply(G, g_rows, n_pad, nplus_w, V32, v_rows, V, v_rows))) return rc;
     }
-    a.G = G; a.V = want_v ? V : nullptr; a.fp32 = 0; a.eps = kEps;
+    a.G = G; a.V = want_v ? V : nullptr; a.fp32 = 0; a.eps = kEps; a.split = split ? 1 : 0;
     int converged = 0, sweeps = 0;
     if ((rc = sweep_loop(o.max_sweeps, &sweeps, &converged))) return rc;
     inf.sweeps = sweeps;
@@ -605,6 +631,7 @@ void jsvd_default_opts(jsvd_opts *o) {
     o->max_sweeps = 30;
     o->precision = JSVD_PREC_FP64;
     o->sort = 1;
+    o->contraction = JSVD_CONTRACT_FP64;
 }
 
 int jsvd_create(jsvd_ctx_t *ctx, int device, void *stream) {

@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "rotation.cuh"
+#include "split_mma.cuh"
 
 namespace jsvd {
 
@@ -58,7 +59,15 @@ constexpr size_t gram_smem_bytes() {
            (Cfg<BB>::kGramSplit > 1 ? sizeof(T) * 4 * Cfg<BB>::kGramSplit * Cfg<BB>::kGramBlocks : 0);
 }
 template <int BB>
-constexpr size_t jacobi_smem_bytes() { return sizeof(double) * 2 * BB * Cfg<BB>::kLd + (BB - 1) * BB + 16; }
+constexpr size_t jacobi_smem_bytes() {
+    // A, B; the Gram diagonal; the column-scale exponents; the inner table
+    return sizeof(double) * (2 * BB * Cfg<BB>::kLd + BB) + sizeof(int) * BB + (BB - 1) * BB + 16;
+}
+
+// Shared-memory / global image of the split digits of a BB x BB right factor
+// (one version): [kSlices][BB rows n][BB + kPad] bf16, K contiguous.
+template <int BB>
+constexpr int split_b_elems() { return split::kSlices * BB * (BB + split::kPad); }
 template <int BB, typename T>
 constexpr size_t update_smem_bytes() { return sizeof(T) * (BB * Cfg<BB>::kUpdRows + BB * (BB + 2)); }
 
@@ -139,6 +148,48 @@ __device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int 
 }
 
 // ---------------------------------------------------------------------------
+// Split digits of the right factors of one pivot pair for the tensor-core
+// update (see split_mma.cuh): version 0 = D V' for [G_P G_Q] with
+// D = diag(2^dexp[j]), 2^dexp[j] ~ sqrt(h_jj) (exact powers of two, so
+// G V' = (G D^-1)(D V')), version 1 = V' for [V_P V_Q].  W is V' in shared
+// memory (column-major, ld BB+1).  Column k of a version gets the exponent
+// bound F_k of its entries and the digits of trunc(x 2^(62-F_k)), stored as
+// out[slice][k][j] (K = j contiguous, row stride BB + kPad).
+template <int BB>
+__device__ __forceinline__ void split_right_factor(const double *W, const double *hdiag, int *dx,
+                                                   uint16_t *__restrict__ out, int *__restrict__ bexp,
+                                                   int *__restrict__ dexp) {
+    using C = Cfg<BB>;
+    constexpr int LD = BB + split::kPad;
+    for (int j = threadIdx.x; j < BB; j += C::kJacThreads) {
+        const double h = hdiag[j];
+        const int d = h > 0.0 ? (split::exp_of(h) >> 1) : 0;
+        dx[j] = d;
+        dexp[j] = d;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * BB; t += C::kJacThreads) {
+        const int ver = t / BB, k = t % BB;
+        const double *w = W + k * C::kLd;
+        int F = split::kNoExp;
+        for (int j = 0; j < BB; ++j) F = max(F, split::exp_bound(w[j], ver ? 0 : dx[j]));
+        if (F == split::kNoExp) F = 0;
+        bexp[ver * BB + k] = F;
+        uint16_t *o = out + (size_t)ver * split_b_elems<BB>() + k * LD;
+        for (int j = 0; j < BB; j += 2) {
+            const unsigned long long z0 = split::fixed_biased(w[j], ver ? 0 : dx[j], F);
+            const unsigned long long z1 = split::fixed_biased(w[j + 1], ver ? 0 : dx[j + 1], F);
+#define JSVD_SPLIT_STORE(I) \
+    *reinterpret_cast<uint32_t *>(o + (I) * BB * LD + j) = \
+        split::pack2(split::digit_bf16<I>(z0), split::digit_bf16<I>(z1));
+            JSVD_SPLIT_STORE(0) JSVD_SPLIT_STORE(1) JSVD_SPLIT_STORE(2) JSVD_SPLIT_STORE(3) JSVD_SPLIT_STORE(4)
+            JSVD_SPLIT_STORE(5) JSVD_SPLIT_STORE(6) JSVD_SPLIT_STORE(7) JSVD_SPLIT_STORE(8)
+#undef JSVD_SPLIT_STORE
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Per-pair factorization and inner sweeps; executed by Cfg<BB>::kJacThreads
 // threads.  smem: A and B, each BB x BB column-major with ld BB+1, then the
 // inner table ((BB-1) x BB/2 pairs of bytes).
@@ -148,7 +199,11 @@ __device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int 
 // (256/BB lanes); lane g of the group owns rows g, g + 256/BB, ... of both
 // columns in R and V'.
 // Writes V' (column-major, BB x BB) to vp and "V' != I" to *vflag; adds the
-// rotation counts to counters[].  Global columns in [bord_lo, bord_hi) are the
+// rotation counts to counters[].  With bsl != null (tensor-core contractions)
+// it also writes, for the update of G, the column scales D = 2^dexp[j] with
+// 2^dexp[j] ~ ||g_j|| (from the Gram diagonal) and the split digits of D V',
+// and for the update of V those of V' (bsl + split_b_elems, bexp + BB); bexp
+// holds each column's exponent bound.  Global columns in [bord_lo, bord_hi) are the
 // identity border: they are exactly orthogonal to everything, and they are
 // neither rotated nor swapped, so they keep their positions.
 template <int BB>
@@ -157,11 +212,14 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
                                             int nplus, int bord_lo, int bord_hi, int inner_sweeps, double eps,
                                             double *__restrict__ vp,
                                             int *__restrict__ vflag, unsigned long long *__restrict__ counters,
-                                            double *smem) {
+                                            double *smem, uint16_t *__restrict__ bsl = nullptr,
+                                            int *__restrict__ bexp = nullptr, int *__restrict__ dexp = nullptr) {
     using C = Cfg<BB>;
     double *A = smem;
     double *B = smem + BB * C::kLd;
-    unsigned char *tab = reinterpret_cast<unsigned char *>(smem + 2 * BB * C::kLd);
+    double *hdiag = smem + 2 * BB * C::kLd;
+    int *dx = reinterpret_cast<int *>(hdiag + BB);
+    unsigned char *tab = reinterpret_cast<unsigned char *>(dx + BB);
     __shared__ double s_piv;
     __shared__ int s_brk;
     __shared__ unsigned long long s_off;
@@ -197,6 +255,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     for (int j = tid; j < BB; j += C::kJacThreads) {
         const double d = A[j + j * C::kLd];
         B[j] = d > 0.0 ? rsqrt(d) : 0.0;
+        hdiag[j] = d;
     }
     __syncthreads();
     {
@@ -319,6 +378,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
         const int i = e % BB, j = e / BB;
         vp[e] = A[i + j * C::kLd];
     }
+    if (bsl && any_change) split_right_factor<BB>(A, hdiag, dx, bsl, bexp, dexp);
     atomicAdd(&s_cnt[0], my_rot);
     atomicAdd(&s_cnt[1], my_proper);
     __syncthreads();

@@ -26,7 +26,8 @@ __global__ void __launch_bounds__(Cfg<BB>::kJacThreads) pair_jacobi(PStepArgs a)
     const int Q = a.table[2 * (a.step * a.npairs + pair) + 1];
     jacobi_unit<BB>(a.part + (size_t)pair * a.g_chunks * Cfg<BB>::kPacked, a.g_chunks, a.inner, P, Q, a.b,
                     a.nplus, a.bord_lo, a.bord_hi, a.inner_sweeps, a.eps, a.vprime + (size_t)pair * BB * BB, a.vflag + pair,
-                    a.counters, smem);
+                    a.counters, smem, a.split ? a.bslice + (size_t)pair * 2 * split_b_elems<BB>() : nullptr,
+                    a.split ? a.bexp + (size_t)pair * 2 * BB : nullptr, a.split ? a.dexp + (size_t)pair * BB : nullptr);
 }
 
 template <int BB, typename T>
@@ -88,6 +89,10 @@ static void launch_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
 }
 
 void launch_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s) {
+    if (a.split && !a.fp32 && ph != Phase::Jacobi) {
+        launch_split_phase(BB, ph, a, s);
+        return;
+    }
     if (a.fp32) {
         switch (BB) {
             case 16: launch_bb<16, float>(ph, a, s); break;

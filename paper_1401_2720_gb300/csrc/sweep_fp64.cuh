@@ -48,6 +48,12 @@ struct PStepArgs {
     double *vprime;         // V' [npairs][BB*BB], column-major
     int *vflag;             // [npairs]: 1 if V' != I
     unsigned long long *counters;  // kCnt* slots
+    // tensor-core contractions (FP64 sweeps only): the Jacobi kernel writes the
+    // split right factors, the Gram and update kernels are the split forms
+    int split;
+    uint16_t *bslice;       // [npairs][2][split_b_elems<BB>] digits (G version, V version)
+    int *bexp;              // [npairs][2][BB] column exponent bounds of the right factors
+    int *dexp;              // [npairs][BB] column scales of [G_P G_Q]
 };
 
 constexpr int kRowAlign = 256;     // g_rows, v_rows are multiples of this
@@ -56,5 +62,7 @@ constexpr int kRowAlign = 256;     // g_rows, v_rows are multiples of this
 // Cholesky + inner sweep, or the update of G, of V, or of both.
 enum class Phase { Gram, Jacobi, UpdateG, UpdateV, UpdateGV };
 void launch_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
+// The tensor-core forms of the Gram and update phases (sweep_split.cu).
+void launch_split_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
 
 }  // namespace jsvd

@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libjsvd.so")
 
 STRATEGIES = {"modulus": 0, "R": 1, "C": 2, "rR": 3, "rC": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+# FP64 block contractions: FP64 FMA kernels, or split bf16 digits on the tensor cores
+CONTRACTIONS = {"fp64": 0, "split": 1}
 STATUS = {0: "success", 1: "not converged", 2: "non-finite input", 3: "CUDA error",
           4: "allocation failed", 5: "unsupported", 6: "device wait timed out",
           7: "too large for the no-allocation entry point"}
@@ -37,7 +39,7 @@ class JsvdError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("strategy", ctypes.c_int), ("inner_strategy", ctypes.c_int),
                 ("inner_sweeps", ctypes.c_int), ("max_sweeps", ctypes.c_int),
-                ("precision", ctypes.c_int), ("sort", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("sort", ctypes.c_int), ("contraction", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -118,7 +120,7 @@ def _raise(rc: int, h) -> None:
 
 def make_opts(b: int = 0, strategy: str = "rR", inner_strategy: str | None = None,
               inner_sweeps: int = 1, max_sweeps: int = 30, precision: str = "fp64",
-              sort: bool = True) -> Opts:
+              sort: bool = True, contraction: str = "fp64") -> Opts:
     o = Opts()
     library().jsvd_default_opts(ctypes.byref(o))
     o.b = b
@@ -128,6 +130,7 @@ def make_opts(b: int = 0, strategy: str = "rR", inner_strategy: str | None = Non
     o.max_sweeps = max_sweeps
     o.precision = PRECISIONS[precision]
     o.sort = 1 if sort else 0
+    o.contraction = CONTRACTIONS[contraction]
     return o
 
 
