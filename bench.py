@@ -472,7 +472,7 @@ def main():
                    help="block width (default 32; the batched workload autotunes it per bucket of n)")
     p.add_argument("--strategy", default=None, help="pivot strategy (default rR; modulus for small512)")
     p.add_argument("--max-sweeps", type=int, default=30)
-    p.add_argument("--contraction", default="fp64", choices=["fp64", "split"],
+    p.add_argument("--contraction", default="split", choices=["fp64", "split"],
                    help="FP64 block contractions: FP64 FMA kernels or split bf16 digits on the tensor cores")
     p.add_argument("--inner-sweeps", type=int, default=1,
                    help="inner sweeps per pivot pair: 1 = block-oriented, 30 = full block (Sec. 4.3)")

@@ -74,7 +74,7 @@ typedef struct {
     int max_sweeps;      /* limit on block sweeps (0: 30) */
     int precision;       /* JSVD_PREC_* */
     int sort;            /* 1: sigma non-increasing (per sign block for the HSVD) */
-    int contraction;     /* JSVD_CONTRACT_*; the batched solver always uses FP64 */
+    int contraction;     /* JSVD_CONTRACT_* (default SPLIT); the batched solver always uses FP64 */
 } jsvd_opts;
 
 typedef struct {

@@ -631,7 +631,7 @@ void jsvd_default_opts(jsvd_opts *o) {
     o->max_sweeps = 30;
     o->precision = JSVD_PREC_FP64;
     o->sort = 1;
-    o->contraction = JSVD_CONTRACT_FP64;
+    o->contraction = JSVD_CONTRACT_SPLIT;
 }
 
 int jsvd_create(jsvd_ctx_t *ctx, int device, void *stream) {

@@ -154,29 +154,44 @@ __device__ __forceinline__ void zero_levels(float (&lev)[kLevels][8]) {
 __device__ __forceinline__ int acc_row(int e) { return ((threadIdx.x & 31) >> 2) + ((e & 2) ? 8 : 0); }
 __device__ __forceinline__ int acc_col(int e) { return 2 * (threadIdx.x & 3) + (e & 1) + ((e & 4) ? 8 : 0); }
 
+// r * 2^s for any s in [-2200, 2200], r finite (the rare path: r = 0, or a
+// result outside the normal range).
+static __device__ __noinline__ double scale_slow(double r, int s) {
+    const int s1 = s / 2, s2 = s - s1;
+    if (s1 < -1022 || s2 < -1022) return __dmul_rn(r, 0.0);
+    return __dmul_rn(__dmul_rn(r, __longlong_as_double((long long)(s1 + 1023) << 52)),
+                     __longlong_as_double((long long)(s2 + 1023) << 52));
+}
+
 // The FP64 value 2^(ea + eb - 40) * sum_L lev[L] 128^(4-L), rounded once.
-// Level values are exact integers with |lev| < 2^23.
+// Level values are exact integers with |lev| < 2^23; with kSmall they are
+// below 2^22 (contraction length <= 64), and the float -> int conversion is
+// one FP32 add of 1.5 * 2^23 (the integer lands in the low significand bits)
+// instead of a quarter-rate conversion instruction.
+template <bool kSmall>
 __device__ __forceinline__ double combine(const float (&lv)[kLevels], int ea, int eb) {
     int v[kLevels];
 #pragma unroll
-    for (int L = 0; L < kLevels; ++L) v[L] = __float2int_rn(lv[L]);
+    for (int L = 0; L < kLevels; ++L)
+        v[L] = kSmall ? __float_as_int(__fadd_rn(lv[L], 12582912.0f)) - 0x4B400000 : __float2int_rn(lv[L]);
     long long hi = v[0];
 #pragma unroll
     for (int L = 1; L < 5; ++L) hi = hi * 128 + v[L];
     long long lo = v[5];
 #pragma unroll
     for (int L = 6; L < kLevels; ++L) lo = lo * 128 + v[L];
-    // |hi| < 2^52, |lo| < 2^45: exact through the 1.5 * 2^52 offset
+    // |hi| < 2^48, |lo| < 2^45: exact through the 1.5 * 2^52 offset
     const double H = __longlong_as_double(0x4338000000000000ll + hi);
     const double Lo = __longlong_as_double(0x4338000000000000ll + lo);
     const double hm = __dsub_rn(H, 0x1.8p52 + 0x1.8p24);            // hi - 1.5 * 2^24, exact
     const double r = __fma_rn(Lo, 0x1p-28, hm);                      // hi + lo 2^-28, one rounding
-    int s = ea + eb - 40;
-    if (s >= -1022 && s <= 1023) return __dmul_rn(r, __longlong_as_double((long long)(s + 1023) << 52));
-    const int s1 = s / 2, s2 = s - s1;
-    if (s1 < -1022 || s2 < -1022) return 0.0 * r;
-    return __dmul_rn(__dmul_rn(r, __longlong_as_double((long long)(s1 + 1023) << 52)),
-                     __longlong_as_double((long long)(s2 + 1023) << 52));
+    // scale by 2^s on the exponent field when r and the result are normal
+    const int s = ea + eb - 40;
+    const long long rb = __double_as_longlong(r);
+    const int ef = (int)((rb >> 52) & 0x7ff);
+    if (ef != 0 && ef + s >= 1 && ef + s <= 2046) return __longlong_as_double(rb + ((long long)s << 52));
+    if ((rb << 1) == 0) return r;
+    return scale_slow(r, s);
 }
 
 }  // namespace split

@@ -18,7 +18,9 @@ template <int BB> struct SplitCfg {
     static constexpr int kGramWarps = kTiles * kKsplit;                // 4, 6, 10
     static constexpr int kGLd = kGramRows + split::kPad;               // digit row stride (K = rows)
     static constexpr int kGSlice = BB * kGLd;
-    static constexpr int kMB = BB == 64 ? 64 : 128;                    // update: rows per block
+    // update: rows per block; at BB = 64, 32 rows keep the CTA's shared memory
+    // small enough for a pair_jacobi CTA to run beside it on the same SM
+    static constexpr int kMB = BB == 64 ? 32 : 128;
     static constexpr int kULd = BB + split::kPad;
     static constexpr int kUSliceA = kMB * kULd;
     static constexpr int kUSliceB = BB * kULd;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kGramWarps) gram_split(PSte
             float lv[split::kLevels];
 #pragma unroll
             for (int L = 0; L < split::kLevels; ++L) lv[L] = lev[L][e];
-            out[packed_lower<BB>(row, col)] = split::combine(lv, cexp[row], cexp[col]);
+            out[packed_lower<BB>(row, col)] = split::combine<false>(lv, cexp[row], cexp[col]);
         }
     }
 }
@@ -142,7 +144,8 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
     constexpr int NW = S::kUpdWarps;
     constexpr int MB = S::kMB;
     constexpr int CPW = BB / NW;          // columns per warp when loading: 8, 4, 2
-    constexpr int RPL = MB / 32;          // rows per lane: 2, 4, 4
+    constexpr int RPL = MB / 32;          // rows per lane: 1, 4, 4
+    static_assert(RPL == 1 || RPL % 2 == 0, "rows per lane");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);
     uint16_t *Bs = As + split::kSlices * S::kUSliceA;
@@ -186,11 +189,15 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
 #pragma unroll
         for (int c = 0; c < CPW; ++c) {
             const double *src = X + (size_t)gcol[c] * ld + rb + lane * RPL;
+            if constexpr (RPL == 1) {
+                x[c][0] = src[0];
+            } else {
 #pragma unroll
-            for (int q = 0; q < RPL; q += 2) {
-                const double2 v = *reinterpret_cast<const double2 *>(src + q);
-                x[c][q] = v.x;
-                x[c][q + 1] = v.y;
+                for (int q = 0; q < RPL; q += 2) {   // RPL even: 16-byte aligned pairs
+                    const double2 v = *reinterpret_cast<const double2 *>(src + q);
+                    x[c][q] = v.x;
+                    x[c][q + 1] = v.y;
+                }
             }
         }
 #pragma unroll
@@ -211,9 +218,9 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
             if (E == split::kNoExp) E = 0;
             if (warp == 0) rexp[r] = E;
             uint16_t *dst = As + r * S::kULd + warp * CPW;
+            if constexpr (CPW >= 4) {
 #pragma unroll
-            for (int c = 0; c < CPW; c += 4) {
-                if (CPW >= 4) {
+                for (int c = 0; c < CPW; c += 4) {
                     const unsigned long long z[4] = {
                         split::fixed_biased(x[c][q], -dexp[warp * CPW + c], E),
                         split::fixed_biased(x[c + 1][q], -dexp[warp * CPW + c + 1], E),
@@ -221,8 +228,8 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
                         split::fixed_biased(x[c + 3][q], -dexp[warp * CPW + c + 3], E)};
                     store_digits4(dst + c, S::kUSliceA, z);
                 }
-            }
-            if (CPW == 2) {
+            } else {
+                static_assert(CPW == 2, "two columns per warp");
                 const unsigned long long z0 = split::fixed_biased(x[0][q], -dexp[warp * CPW], E);
                 const unsigned long long z1 = split::fixed_biased(x[CPW - 1][q], -dexp[warp * CPW + 1], E);
 #define JSVD_D2(I) \
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
                 float lv[split::kLevels];
 #pragma unroll
                 for (int L = 0; L < split::kLevels; ++L) lv[L] = lev[L][e];
-                X[(size_t)block_col(P, Q, a.b, col) * ld + rb + row] = split::combine(lv, rexp[row], fexp[col]);
+                X[(size_t)block_col(P, Q, a.b, col) * ld + rb + row] = split::combine<true>(lv, rexp[row], fexp[col]);
             }
         }
         __syncthreads();

@@ -120,7 +120,7 @@ def _raise(rc: int, h) -> None:
 
 def make_opts(b: int = 0, strategy: str = "rR", inner_strategy: str | None = None,
               inner_sweeps: int = 1, max_sweeps: int = 30, precision: str = "fp64",
-              sort: bool = True, contraction: str = "fp64") -> Opts:
+              sort: bool = True, contraction: str = "split") -> Opts:
     o = Opts()
     library().jsvd_default_opts(ctypes.byref(o))
     o.b = b

@@ -44,12 +44,13 @@ def test_batched_against_oracle(cuda, b):
 
 def test_batched_equals_single_path(cuda):
     """Same block width and ordering: the batched solver performs the single
-    path's arithmetic (extra zero rows only add exact zeros), bit for bit."""
+    path's arithmetic with the FP64 FMA contractions (extra zero rows only add
+    exact zeros), bit for bit."""
     mats, _, _, _ = _batch(12, seed=2)
     pk = J.Packing([a.shape[0] for a in mats], [a.shape[1] for a in mats])
     U, S, V = J.svd_batched_packed(pk, pk.pack(mats, cuda), b=8)
     for a, u, s, v in zip(mats, pk.unpack_mn(U), pk.unpack_n(S), pk.unpack_nn(V)):
-        u1, s1, v1 = J.svd(_t(a, cuda), b=8)
+        u1, s1, v1 = J.svd(_t(a, cuda), b=8, contraction="fp64")
         assert torch.equal(s, s1) and torch.equal(u, u1) and torch.equal(v, v1)
 
 

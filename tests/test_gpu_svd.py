@@ -56,9 +56,10 @@ def test_rotation_params_bitwise(cuda):
         assert np.array_equal(_np(pr), pr_o)
 
 
+@pytest.mark.parametrize("contraction", ["fp64", "split"])
 @pytest.mark.parametrize("b", [8, 16, 32])
 @pytest.mark.parametrize("sweeps", [1, 2])
-def test_block_sweeps_elementwise(cuda, b, sweeps):
+def test_block_sweeps_elementwise(cuda, b, sweeps, contraction):
     """After k block sweeps (no sorting of the output), G = U S and V agree
     element by element with the oracle's block-oriented method.  The columns
     are graded (norms 1 .. 1e-4) so that no two column norms nearly tie: a
@@ -70,7 +71,7 @@ def test_block_sweeps_elementwise(cuda, b, sweeps):
     A = np.asfortranarray(rng.standard_normal((m, n)) * (10.0 ** (-4.0 * np.arange(n) / (n - 1)))[None, :])
     r = O.block_svd(A, b, strategy="rR", max_sweeps=sweeps)
     U, S, V, info = J.svd(_t(A, cuda), b=b, strategy="rR", max_sweeps=sweeps, sort=False,
-                          return_info=True)
+                          return_info=True, contraction=contraction)
     assert info["sweeps"] == sweeps
     G = _np(U) * _np(S)[None, :]
     scale = np.linalg.norm(A, 2)
