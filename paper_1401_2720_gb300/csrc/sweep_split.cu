@@ -18,14 +18,17 @@ template <int BB> struct SplitCfg {
     static constexpr int kGramWarps = kTiles * kKsplit;                // 4, 6, 10
     static constexpr int kGLd = kGramRows + split::kPad;               // digit row stride (K = rows)
     static constexpr int kGSlice = BB * kGLd;
-    // update: rows per block; at BB = 64, 32 rows keep the CTA's shared memory
-    // small enough for a pair_jacobi CTA to run beside it on the same SM
-    static constexpr int kMB = BB == 64 ? 32 : 128;
+    // update: 4 producer warps (load, exponents, digits) and 4 consumer warps
+    // (one 16x16 output tile each) over double-buffered blocks of kMB rows;
+    // every producer thread holds 8 entries of a block (one row, 8 columns)
+    static constexpr int kCG = BB / 8;                                 // column groups of 8
+    static constexpr int kMB = 128 / kCG;                              // rows per block: 16, 32, 64
     static constexpr int kULd = BB + split::kPad;
     static constexpr int kUSliceA = kMB * kULd;
     static constexpr int kUSliceB = BB * kULd;
     static constexpr int kUpdWarps = 8;
     static constexpr int kUpdRowsPerCta = 512;                         // rows of one update CTA
+    static_assert((kMB / 16) * (BB / 16) == 4, "one tile per consumer warp");
 };
 
 template <int BB>
@@ -37,7 +40,7 @@ constexpr size_t gram_split_smem() {
 template <int BB>
 constexpr size_t update_split_smem() {
     using S = SplitCfg<BB>;
-    return 2u * split::kSlices * (S::kUSliceA + S::kUSliceB) + sizeof(int) * (2 * BB + (S::kUpdWarps + 1) * S::kMB);
+    return 2u * split::kSlices * (2 * S::kUSliceA + S::kUSliceB) + sizeof(int) * (2 * BB + 2 * (S::kCG + 1) * S::kMB);
 }
 
 // Store the 9 digits of 4 consecutive K entries (one 8-byte store per slice).
@@ -138,21 +141,49 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kGramWarps) gram_split(PSte
 // operand is G D^-1 (D from the pair's Gram diagonal) against the digits of
 // D V'; for V it is V against those of V'.  Row r of a block gets the exponent
 // bound E_r of its BB entries; X(r, k) = 2^(E_r + F_k - 40) * combine(levels).
+//
+// Warps 0-3 produce: load block t (thread p: row p % kMB, columns
+// 8 (p / kMB) .. +7), reduce the row exponents, write the digits to buffer
+// t % 2, and arrive on FULL(t % 2).  Warps 4-7 consume: wait on FULL, run the
+// level MMAs of their tile, read the tile rows' exponents, arrive on EMPTY
+// (which the producers wait on before refilling that buffer two blocks
+// later), then combine and store.  Named barriers with matched counts: every
+// producer and consumer thread runs the same number of blocks.
+namespace nb {
+constexpr int kFull0 = 1, kEmpty0 = 3, kProd = 5;   // ids 1-2 FULL, 3-4 EMPTY, 5 producers only
+}
+template <int ID, int COUNT>
+__device__ __forceinline__ void bar_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
+}
+template <int ID, int COUNT>
+__device__ __forceinline__ void bar_arrive() {
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
+}
+// barrier of buffer buf (0 or 1) with immediate ids
+template <int ID0, int COUNT>
+__device__ __forceinline__ void bar_sync_buf(int buf) {
+    if (buf) bar_sync<ID0 + 1, COUNT>(); else bar_sync<ID0, COUNT>();
+}
+template <int ID0, int COUNT>
+__device__ __forceinline__ void bar_arrive_buf(int buf) {
+    if (buf) bar_arrive<ID0 + 1, COUNT>(); else bar_arrive<ID0, COUNT>();
+}
+
 template <int BB>
 __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PStepArgs a, int g_units) {
     using S = SplitCfg<BB>;
-    constexpr int NW = S::kUpdWarps;
     constexpr int MB = S::kMB;
-    constexpr int CPW = BB / NW;          // columns per warp when loading: 8, 4, 2
-    constexpr int RPL = MB / 32;          // rows per lane: 1, 4, 4
-    static_assert(RPL == 1 || RPL % 2 == 0, "rows per lane");
+    constexpr int CG = S::kCG;
+    constexpr int NT = 32 * S::kUpdWarps;             // 256
+    constexpr int NP = NT / 2;                         // producer threads
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);
-    uint16_t *Bs = As + split::kSlices * S::kUSliceA;
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                 // [2][kSlices][MB][kULd]
+    uint16_t *Bs = As + 2 * split::kSlices * S::kUSliceA;                   // [kSlices][BB][kULd]
     int *fexp = reinterpret_cast<int *>(Bs + split::kSlices * S::kUSliceB);
     int *dexp = fexp + BB;
-    int *rmax = dexp + BB;                // [NW][MB]
-    int *rexp = rmax + NW * MB;           // [MB]
+    int *rmax = dexp + BB;                // [2][CG][MB]
+    int *rexp = rmax + 2 * CG * MB;       // [2][MB]
 
     const int pair = blockIdx.y;
     if (!a.vflag[pair]) return;
@@ -164,99 +195,97 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
     const int ld = ver ? a.ldv : a.ldg;
     const int rows = ver ? a.v_rows : a.g_rows;
     const int rbeg = unit * S::kUpdRowsPerCta;
-    const int rend = min(rows, rbeg + S::kUpdRowsPerCta);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nblk = (min(rows, rbeg + S::kUpdRowsPerCta) - rbeg) / MB;   // rows is a multiple of 256
 
     // right factor digits and exponents of this pair and version
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.bslice + ((size_t)pair * 2 + ver) * split_b_elems<BB>());
         uint4 *dst = reinterpret_cast<uint4 *>(Bs);
-        for (int e = threadIdx.x; e < split_b_elems<BB>() / 8; e += 32 * NW) dst[e] = src[e];
-        for (int k = threadIdx.x; k < BB; k += 32 * NW) {
+        for (int e = threadIdx.x; e < split_b_elems<BB>() / 8; e += NT) dst[e] = src[e];
+        for (int k = threadIdx.x; k < BB; k += NT) {
             fexp[k] = a.bexp[((size_t)pair * 2 + ver) * BB + k];
             dexp[k] = ver ? 0 : a.dexp[(size_t)pair * BB + k];
         }
     }
     __syncthreads();
 
-    int gcol[CPW];
+    if (threadIdx.x < NP) {
+        // ---------------- producers ----------------
+        const int p = threadIdx.x;
+        const int r = p % MB, cg = p / MB;
+        const double *src0 = X + rbeg + r;
+        size_t coff[8];
+        int dx[8];
 #pragma unroll
-    for (int c = 0; c < CPW; ++c) gcol[c] = block_col(P, Q, a.b, warp * CPW + c);
-
-    for (int rb = rbeg; rb < rend; rb += MB) {
-        // (1) load: warp w takes columns [w CPW, (w+1) CPW), lane rows rb + lane RPL + q
-        double x[CPW][RPL];
-#pragma unroll
-        for (int c = 0; c < CPW; ++c) {
-            const double *src = X + (size_t)gcol[c] * ld + rb + lane * RPL;
-            if constexpr (RPL == 1) {
-                x[c][0] = src[0];
-            } else {
-#pragma unroll
-                for (int q = 0; q < RPL; q += 2) {   // RPL even: 16-byte aligned pairs
-                    const double2 v = *reinterpret_cast<const double2 *>(src + q);
-                    x[c][q] = v.x;
-                    x[c][q + 1] = v.y;
-                }
-            }
+        for (int c = 0; c < 8; ++c) {
+            coff[c] = (size_t)block_col(P, Q, a.b, 8 * cg + c) * ld;
+            dx[c] = dexp[8 * cg + c];
         }
+        double x[8];
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) {
+        for (int c = 0; c < 8; ++c) x[c] = src0[coff[c]];
+        for (int t = 0; t < nblk; ++t) {
+            const int buf = t & 1;
             int m = split::kNoExp;
 #pragma unroll
-            for (int c = 0; c < CPW; ++c) m = max(m, split::exp_bound(x[c][q], -dexp[warp * CPW + c]));
-            rmax[warp * MB + lane * RPL + q] = m;
-        }
-        __syncthreads();
-        // (2) row exponent bounds and digits of x 2^-dexp
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            const int r = lane * RPL + q;
+            for (int c = 0; c < 8; ++c) m = max(m, split::exp_bound(x[c], -dx[c]));
+            rmax[(buf * CG + cg) * MB + r] = m;
+            bar_sync<nb::kProd, NP>();
             int E = split::kNoExp;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) E = max(E, rmax[w * MB + r]);
+            for (int g = 0; g < CG; ++g) E = max(E, rmax[(buf * CG + g) * MB + r]);
             if (E == split::kNoExp) E = 0;
-            if (warp == 0) rexp[r] = E;
-            uint16_t *dst = As + r * S::kULd + warp * CPW;
-            if constexpr (CPW >= 4) {
+            unsigned long long z[8];
 #pragma unroll
-                for (int c = 0; c < CPW; c += 4) {
-                    const unsigned long long z[4] = {
-                        split::fixed_biased(x[c][q], -dexp[warp * CPW + c], E),
-                        split::fixed_biased(x[c + 1][q], -dexp[warp * CPW + c + 1], E),
-                        split::fixed_biased(x[c + 2][q], -dexp[warp * CPW + c + 2], E),
-                        split::fixed_biased(x[c + 3][q], -dexp[warp * CPW + c + 3], E)};
-                    store_digits4(dst + c, S::kUSliceA, z);
-                }
-            } else {
-                static_assert(CPW == 2, "two columns per warp");
-                const unsigned long long z0 = split::fixed_biased(x[0][q], -dexp[warp * CPW], E);
-                const unsigned long long z1 = split::fixed_biased(x[CPW - 1][q], -dexp[warp * CPW + 1], E);
-#define JSVD_D2(I) \
-    *reinterpret_cast<uint32_t *>(dst + (I) * S::kUSliceA) = split::pack2(split::digit_bf16<I>(z0), split::digit_bf16<I>(z1));
-                JSVD_D2(0) JSVD_D2(1) JSVD_D2(2) JSVD_D2(3) JSVD_D2(4) JSVD_D2(5) JSVD_D2(6) JSVD_D2(7) JSVD_D2(8)
-#undef JSVD_D2
+            for (int c = 0; c < 8; ++c) z[c] = split::fixed_biased(x[c], -dx[c], E);
+            // prefetch the next block's entries while this one is split
+            if (t + 1 < nblk) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) x[c] = src0[coff[c] + (size_t)(t + 1) * MB];
             }
+            if (t >= 2) bar_sync_buf<nb::kEmpty0, NT>(buf);   // consumers are done with block t - 2
+            if (cg == 0) rexp[buf * MB + r] = E;
+            uint16_t *dst = As + (size_t)buf * split::kSlices * S::kUSliceA + r * S::kULd + 8 * cg;
+            const unsigned long long z0[4] = {z[0], z[1], z[2], z[3]};
+            const unsigned long long z1[4] = {z[4], z[5], z[6], z[7]};
+            store_digits4(dst, S::kUSliceA, z0);
+            store_digits4(dst + 4, S::kUSliceA, z1);
+            bar_arrive_buf<nb::kFull0, NT>(buf);
         }
-        __syncthreads();
-        // (3) 16x16 output tiles over the warps; combine and store to X
-        constexpr int TM = MB / 16, TN = BB / 16;
-        for (int t = warp; t < TM * TN; t += NW) {
-            const int tm = t / TN, tn = t % TN;
+    } else {
+        // ---------------- consumers ----------------
+        const int cw = (threadIdx.x - NP) >> 5;        // 0..3: tile
+        constexpr int TN = BB / 16;
+        const int tm = cw / TN, tn = cw % TN;
+        int gcol[8];
+        int fx[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int col = tn * 16 + split::acc_col(e);
+            gcol[e] = block_col(P, Q, a.b, col);
+            fx[e] = fexp[col];
+        }
+        for (int t = 0; t < nblk; ++t) {
+            const int buf = t & 1;
+            bar_sync_buf<nb::kFull0, NT>(buf);
             float lev[split::kLevels][8];
             split::zero_levels(lev);
-            split::tile_levels<BB / 16>(As + tm * 16 * S::kULd, S::kULd, S::kUSliceA, Bs + tn * 16 * S::kULd, S::kULd,
+            const uint16_t *Ab = As + (size_t)buf * split::kSlices * S::kUSliceA;
+            split::tile_levels<BB / 16>(Ab + tm * 16 * S::kULd, S::kULd, S::kUSliceA, Bs + tn * 16 * S::kULd, S::kULd,
                                         S::kUSliceB, lev);
+            const int r0 = tm * 16 + split::acc_row(0), r1 = tm * 16 + split::acc_row(2);
+            const int e0 = rexp[buf * MB + r0], e1 = rexp[buf * MB + r1];
+            if (t + 2 < nblk) bar_arrive_buf<nb::kEmpty0, NT>(buf);
+            const size_t rb = (size_t)rbeg + (size_t)t * MB;
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const int row = tm * 16 + split::acc_row(e), col = tn * 16 + split::acc_col(e);
                 float lv[split::kLevels];
 #pragma unroll
                 for (int L = 0; L < split::kLevels; ++L) lv[L] = lev[L][e];
-                X[(size_t)block_col(P, Q, a.b, col) * ld + rb + row] = split::combine<true>(lv, rexp[row], fexp[col]);
+                const int row = (e & 2) ? r1 : r0;
+                X[(size_t)gcol[e] * ld + rb + row] = split::combine<true>(lv, (e & 2) ? e1 : e0, fx[e]);
             }
         }
-        __syncthreads();
     }
 }
 
