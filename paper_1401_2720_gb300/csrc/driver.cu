@@ -228,7 +228,7 @@ int jsvd_ctx::inner_table(int strategy, int BB, const unsigned char **dev) {
 }
 
 jsvd_ctx::~jsvd_ctx() {
-    for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp,
+    for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp, &gexp,
                       &g32, &v32,
                       &tmp_a, &tmp_b, &tmp_g, &b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag,
                       &b_tab, &b_cnt, &b_stat, &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &adj_w,
@@ -406,6 +406,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         if ((rc = ensure(bslice, sizeof(uint16_t) * bsl_pairs * ring))) return rc;
         if ((rc = ensure(bexp, sizeof(int) * (size_t)npairs * 2 * BB * ring))) return rc;
         if ((rc = ensure(dexp, sizeof(int) * (size_t)npairs * BB * ring))) return rc;
+        if ((rc = ensure(gexp, sizeof(int) * (size_t)n_pad))) return rc;
     }
     if (side_streams && (rc = ensure_side_stream())) return rc;
     if ((rc = ensure(counters, sizeof(unsigned long long) * kCntSize))) return rc;
@@ -574,6 +575,13 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         if ((rc = polar_and_apply(G, g_rows, n_pad, nplus_w, V32, v_rows, V, v_rows))) return rc;
     }
     a.G = G; a.V = want_v ? V : nullptr; a.fp32 = 0; a.eps = kEps; a.split = split ? 1 : 0;
+    if (split) {
+        // Gram partials of 256 rows; column exponent bounds of the current G
+        a.g_chunks = g_rows / kGramRowsSplit;
+        a.gexp = (int *)gexp.ptr;
+        launch_col_maxexp(G, g_rows, g_rows, n_pad, a.gexp, stream);
+        prof_launches[4] += 1;
+    }
     int converged = 0, sweeps = 0;
     if ((rc = sweep_loop(o.max_sweeps, &sweeps, &converged))) return rc;
     inf.sweeps = sweeps;

@@ -22,7 +22,7 @@ struct jsvd_ctx {
 
     // workspace (grown on demand, freed with the context)
     Buffer g, v, part, vprime, vflag, counters, sigma, border, perm;
-    Buffer bslice, bexp, dexp;             // split right factors (tensor-core contractions)
+    Buffer bslice, bexp, dexp, gexp;       // split right factors, column exponent bounds (tensor-core contractions)
     Buffer g32, v32, tmp_a, tmp_b, tmp_g;  // mixed precision
     Buffer b_mats, b_units, b_g, b_v, b_part, b_vp, b_vflag, b_tab, b_cnt, b_stat, b_starts, b_sigma,
         b_border, b_perm, b_misc;          // batched solver

@@ -56,7 +56,7 @@ struct NoallocCtx : jsvd_ctx {
     ~NoallocCtx() override {
         // nothing was allocated: detach the carved buffers so that the base
         // destructor frees nothing
-        for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp,
+        for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp, &gexp,
                           &g32, &v32, &tmp_a,
                           &tmp_b, &tmp_g, &b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag, &b_tab, &b_cnt,
                           &b_stat, &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &adj_w, &adj_meta,

@@ -203,7 +203,8 @@ __device__ __forceinline__ void split_right_factor(const double *W, const double
 // it also writes, for the update of G, the column scales D = 2^dexp[j] with
 // 2^dexp[j] ~ ||g_j|| (from the Gram diagonal) and the split digits of D V',
 // and for the update of V those of V' (bsl + split_b_elems, bexp + BB); bexp
-// holds each column's exponent bound.  Global columns in [bord_lo, bord_hi) are the
+// holds each column's exponent bound.  With gexp != null the exponent bounds
+// of the pair's columns of G are reset (the split update recomputes them).  Global columns in [bord_lo, bord_hi) are the
 // identity border: they are exactly orthogonal to everything, and they are
 // neither rotated nor swapped, so they keep their positions.
 template <int BB>
@@ -213,7 +214,8 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
                                             double *__restrict__ vp,
                                             int *__restrict__ vflag, unsigned long long *__restrict__ counters,
                                             double *smem, uint16_t *__restrict__ bsl = nullptr,
-                                            int *__restrict__ bexp = nullptr, int *__restrict__ dexp = nullptr) {
+                                            int *__restrict__ bexp = nullptr, int *__restrict__ dexp = nullptr,
+                                            int *__restrict__ gexp = nullptr) {
     using C = Cfg<BB>;
     double *A = smem;
     double *B = smem + BB * C::kLd;
@@ -379,6 +381,9 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
         vp[e] = A[i + j * C::kLd];
     }
     if (bsl && any_change) split_right_factor<BB>(A, hdiag, dx, bsl, bexp, dexp);
+    // the update of G rewrites these columns and max-reduces their new bounds
+    if (gexp && any_change)
+        for (int k = tid; k < BB; k += C::kJacThreads) gexp[block_col(P, Q, b, k)] = split::kNoExp;
     atomicAdd(&s_cnt[0], my_rot);
     atomicAdd(&s_cnt[1], my_proper);
     __syncthreads();

@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(Cfg<BB>::kJacThreads) pair_jacobi(PStepArgs a)
     jacobi_unit<BB>(a.part + (size_t)pair * a.g_chunks * Cfg<BB>::kPacked, a.g_chunks, a.inner, P, Q, a.b,
                     a.nplus, a.bord_lo, a.bord_hi, a.inner_sweeps, a.eps, a.vprime + (size_t)pair * BB * BB, a.vflag + pair,
                     a.counters, smem, a.split ? a.bslice + (size_t)pair * 2 * split_b_elems<BB>() : nullptr,
-                    a.split ? a.bexp + (size_t)pair * 2 * BB : nullptr, a.split ? a.dexp + (size_t)pair * BB : nullptr);
+                    a.split ? a.bexp + (size_t)pair * 2 * BB : nullptr, a.split ? a.dexp + (size_t)pair * BB : nullptr,
+                    a.split ? a.gexp : nullptr);
 }
 
 template <int BB, typename T>

@@ -54,7 +54,10 @@ struct PStepArgs {
     uint16_t *bslice;       // [npairs][2][split_b_elems<BB>] digits (G version, V version)
     int *bexp;              // [npairs][2][BB] column exponent bounds of the right factors
     int *dexp;              // [npairs][BB] column scales of [G_P G_Q]
+    int *gexp;              // [n_pad] exponent bound of every column of G: |g_ij| < 2^gexp[j]
 };
+
+constexpr int kGramRowsSplit = 256;   // rows per Gram partial of the split form (g_rows is a multiple)
 
 constexpr int kRowAlign = 256;     // g_rows, v_rows are multiples of this
 
@@ -64,5 +67,7 @@ enum class Phase { Gram, Jacobi, UpdateG, UpdateV, UpdateGV };
 void launch_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
 // The tensor-core forms of the Gram and update phases (sweep_split.cu).
 void launch_split_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
+// gexp[j] = exponent bound of column j of G (rows [0, rows)), one CTA per column.
+void launch_col_maxexp(const double *G, int ldg, int rows, int ncols, int *gexp, cudaStream_t s);
 
 }  // namespace jsvd

@@ -13,11 +13,21 @@
 namespace jsvd {
 
 template <int BB> struct SplitCfg {
-    static constexpr int kTiles = (BB / 16) * (BB / 16 + 1) / 2;       // lower-triangle 16x16 tiles: 1, 3, 10
-    static constexpr int kKsplit = BB == 64 ? 1 : (BB == 32 ? 2 : 4);  // K parts per tile (warps per tile)
-    static constexpr int kGramWarps = kTiles * kKsplit;                // 4, 6, 10
-    static constexpr int kGLd = kGramRows + split::kPad;               // digit row stride (K = rows)
+    // Gram: 2 producer warps split sub-chunks of kSub rows into a second
+    // buffer while kTiles x kKsplit consumer warps accumulate the levels of
+    // the lower-triangle 16x16 tiles; a tile's K range (the sub-chunks) is
+    // dealt over kKsplit warps.  One partial per kGramRowsSplit rows.  At
+    // most 12 warps: registers are split over the 4 SM sub-partitions.
+    static constexpr int kTiles = (BB / 16) * (BB / 16 + 1) / 2;       // 1, 3, 10
+    static constexpr int kKsplit = BB == 64 ? 1 : (BB == 32 ? 2 : 4);
+    static constexpr int kGCons = kTiles * kKsplit;                    // consumer warps: 4, 6, 10
+    static constexpr int kGThreads = 32 * (kGCons + 2);
+    static constexpr int kSub = 32;
+    static constexpr int kSubsPerChunk = kGramRowsSplit / kSub;        // 8
+    static constexpr int kChunksPerCta = 2;
+    static constexpr int kGLd = kSub + split::kPad;                    // 40
     static constexpr int kGSlice = BB * kGLd;
+    static constexpr int kCPT = BB / 4;                                // columns per producer thread
     // update: 4 producer warps (load, exponents, digits) and 4 consumer warps
     // (one 16x16 output tile each) over double-buffered blocks of kMB rows;
     // every producer thread holds 8 entries of a block (one row, 8 columns)
@@ -34,7 +44,7 @@ template <int BB> struct SplitCfg {
 template <int BB>
 constexpr size_t gram_split_smem() {
     using S = SplitCfg<BB>;
-    return 2u * split::kSlices * S::kGSlice + sizeof(int) * BB +
+    return 2u * 2 * split::kSlices * S::kGSlice + sizeof(int) * BB +
            sizeof(float) * (S::kKsplit - 1) * S::kTiles * split::kLevels * 8 * 32;
 }
 template <int BB>
@@ -53,104 +63,9 @@ __device__ __forceinline__ void store_digits4(uint16_t *dst, int slice_stride, c
 #undef JSVD_D4
 }
 
-// ---------------------------------------------------------------------------
-// Gram partial of one 128-row chunk of [G_P G_Q] (lower triangle, packed),
-// grid (chunks, pairs).  Column c of the chunk gets the exponent bound E_c of
-// its 128 entries; H(j, k) = 2^(E_j + E_k - 40) * combine(levels).
-template <int BB>
-__global__ void __launch_bounds__(32 * SplitCfg<BB>::kGramWarps) gram_split(PStepArgs a) {
-    using S = SplitCfg<BB>;
-    constexpr int NW = S::kGramWarps;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint16_t *Dg = reinterpret_cast<uint16_t *>(smem_raw);
-    int *cexp = reinterpret_cast<int *>(smem_raw + 2u * split::kSlices * S::kGSlice);
-    float *red = reinterpret_cast<float *>(cexp + BB);
-
-    const int pair = blockIdx.y, chunk = blockIdx.x;
-    const int P = a.table[2 * (a.step * a.npairs + pair)];
-    const int Q = a.table[2 * (a.step * a.npairs + pair) + 1];
-    const double *G = reinterpret_cast<const double *>(a.G);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = chunk * kGramRows;
-
-    // (1) one warp per column: 128 rows (4 per lane), exponent bound, digits
-    for (int c = warp; c < BB; c += NW) {
-        const double *col = G + (size_t)block_col(P, Q, a.b, c) * a.ldg + r0 + 4 * lane;
-        const double2 x01 = *reinterpret_cast<const double2 *>(col);
-        const double2 x23 = *reinterpret_cast<const double2 *>(col + 2);
-        int E = max(max(split::exp_bound(x01.x, 0), split::exp_bound(x01.y, 0)),
-                    max(split::exp_bound(x23.x, 0), split::exp_bound(x23.y, 0)));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-        if (E == split::kNoExp) E = 0;
-        const unsigned long long z[4] = {split::fixed_biased(x01.x, 0, E), split::fixed_biased(x01.y, 0, E),
-                                         split::fixed_biased(x23.x, 0, E), split::fixed_biased(x23.y, 0, E)};
-        store_digits4(Dg + c * S::kGLd + 4 * lane, S::kGSlice, z);
-        if (lane == 0) cexp[c] = E;
-    }
-    __syncthreads();
-
-    // (2) warp -> (lower tile t, K part); levels over its K range
-    const int t = warp % S::kTiles, kpart = warp / S::kTiles;
-    int I = 0;
-    while ((I + 1) * (I + 2) / 2 <= t) ++I;
-    const int J = t - I * (I + 1) / 2;
-    constexpr int KSTEPS = kGramRows / 16 / S::kKsplit;
-    float lev[split::kLevels][8];
-    split::zero_levels(lev);
-    const int k0 = kpart * 16 * KSTEPS;
-    split::tile_levels<KSTEPS>(Dg + I * 16 * S::kGLd + k0, S::kGLd, S::kGSlice, Dg + J * 16 * S::kGLd + k0, S::kGLd,
-                               S::kGSlice, lev);
-    if (S::kKsplit > 1) {
-        // the K parts' level sums are exact integers: add them in part order
-        float *mine = red + (((size_t)(kpart - 1) * S::kTiles + t) * split::kLevels * 8) * 32 + lane;
-        if (kpart > 0) {
-#pragma unroll
-            for (int L = 0; L < split::kLevels; ++L)
-#pragma unroll
-                for (int e = 0; e < 8; ++e) mine[(L * 8 + e) * 32] = lev[L][e];
-        }
-        __syncthreads();
-        if (kpart == 0) {
-            for (int p = 1; p < S::kKsplit; ++p) {
-                const float *src = red + (((size_t)(p - 1) * S::kTiles + t) * split::kLevels * 8) * 32 + lane;
-#pragma unroll
-                for (int L = 0; L < split::kLevels; ++L)
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) lev[L][e] += src[(L * 8 + e) * 32];
-            }
-        }
-    }
-    if (kpart == 0) {
-        double *out = a.part + ((size_t)pair * a.g_chunks + chunk) * Cfg<BB>::kPacked;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int row = I * 16 + split::acc_row(e), col = J * 16 + split::acc_col(e);
-            if (row < col) continue;
-            float lv[split::kLevels];
-#pragma unroll
-            for (int L = 0; L < split::kLevels; ++L) lv[L] = lev[L][e];
-            out[packed_lower<BB>(row, col)] = split::combine<false>(lv, cexp[row], cexp[col]);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// [X_P X_Q] := [X_P X_Q] V' on split digits, grid (units, pairs); a unit is
-// kUpdRowsPerCta rows of G (blockIdx.x < g_units) or of V.  For G the A
-// operand is G D^-1 (D from the pair's Gram diagonal) against the digits of
-// D V'; for V it is V against those of V'.  Row r of a block gets the exponent
-// bound E_r of its BB entries; X(r, k) = 2^(E_r + F_k - 40) * combine(levels).
-//
-// Warps 0-3 produce: load block t (thread p: row p % kMB, columns
-// 8 (p / kMB) .. +7), reduce the row exponents, write the digits to buffer
-// t % 2, and arrive on FULL(t % 2).  Warps 4-7 consume: wait on FULL, run the
-// level MMAs of their tile, read the tile rows' exponents, arrive on EMPTY
-// (which the producers wait on before refilling that buffer two blocks
-// later), then combine and store.  Named barriers with matched counts: every
-// producer and consumer thread runs the same number of blocks.
+// Named barriers of the producer/consumer kernels (id 0 is __syncthreads).
 namespace nb {
-constexpr int kFull0 = 1, kEmpty0 = 3, kProd = 5;   // ids 1-2 FULL, 3-4 EMPTY, 5 producers only
+constexpr int kFull0 = 1, kEmpty0 = 3, kProd = 5, kCons = 6;   // 1-2 FULL, 3-4 EMPTY, 5 producers, 6 consumers
 }
 template <int ID, int COUNT>
 __device__ __forceinline__ void bar_sync() {
@@ -170,6 +85,179 @@ __device__ __forceinline__ void bar_arrive_buf(int buf) {
     if (buf) bar_arrive<ID0 + 1, COUNT>(); else bar_arrive<ID0, COUNT>();
 }
 
+// ---------------------------------------------------------------------------
+// Exponent bound of every column of G: gexp[j] = max_i exp_bound(G(i, j)),
+// one CTA per column.  Seeds the bounds at the start of the FP64 sweeps; the
+// split update keeps them current afterwards.
+__global__ void k_col_maxexp(const double *__restrict__ G, int ldg, int rows, int *__restrict__ gexp) {
+    __shared__ int red[32];
+    const double *col = G + (size_t)blockIdx.x * ldg;
+    int m = split::kNoExp;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) m = max(m, split::exp_bound(col[r], 0));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : split::kNoExp;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) gexp[blockIdx.x] = m;
+    }
+}
+
+void launch_col_maxexp(const double *G, int ldg, int rows, int ncols, int *gexp, cudaStream_t s) {
+    k_col_maxexp<<<ncols, 256, 0, s>>>(G, ldg, rows, gexp);
+}
+
+// ---------------------------------------------------------------------------
+// Gram partials of [G_P G_Q] (lower triangle, packed), one per 256 rows,
+// grid (ceil(chunks / kChunksPerCta), pairs).  Column c's scale is its
+// exponent bound E_c = gexp[c]; H(j, k) = 2^(E_j + E_k - 40) * combine(levels),
+// the levels summed exactly over the 256 rows (each partial sum is below
+// 9 * 256 * 64^2 < 2^24).
+//
+// Warps 0-1 produce: thread p takes rows 2 (p % 16), +1 of a 32-row
+// sub-chunk and columns kCPT (p / 16) .. +kCPT-1, writes their digits to
+// buffer s % 2 and arrives on FULL.  Consumer warp w owns tile w % kTiles for
+// the sub-chunks s with s % kKsplit == w / kTiles; after a chunk's last
+// sub-chunk the K parts are added through shared memory (consumers-only
+// barrier) and part 0 combines and stores.
+template <int BB>
+__global__ void __launch_bounds__(SplitCfg<BB>::kGThreads, 1) gram_split(PStepArgs a) {
+    using S = SplitCfg<BB>;
+    constexpr int NT = S::kGThreads;
+    constexpr int NP = 64;
+    constexpr int NC = NT - NP;
+    constexpr int CPT = S::kCPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t *Dg = reinterpret_cast<uint16_t *>(smem_raw);                       // [2][kSlices][BB][kGLd]
+    int *cexp = reinterpret_cast<int *>(Dg + 2 * split::kSlices * S::kGSlice);
+    float *red = reinterpret_cast<float *>(cexp + BB);
+
+    const int pair = blockIdx.y;
+    const int P = a.table[2 * (a.step * a.npairs + pair)];
+    const int Q = a.table[2 * (a.step * a.npairs + pair) + 1];
+    const double *G = reinterpret_cast<const double *>(a.G);
+    const int chunk0 = blockIdx.x * S::kChunksPerCta;
+    const int nchunks = min(S::kChunksPerCta, a.g_chunks - chunk0);
+    const int nsub = nchunks * S::kSubsPerChunk;
+    const size_t row0 = (size_t)chunk0 * kGramRowsSplit;
+
+    for (int c = threadIdx.x; c < BB; c += NT) {
+        const int e = a.gexp[block_col(P, Q, a.b, c)];
+        cexp[c] = e == split::kNoExp ? 0 : e;
+    }
+    __syncthreads();
+
+    if (threadIdx.x < NP) {
+        // ---------------- producers ----------------
+        const int p = threadIdx.x;
+        const int rp = p & 15, cg = p >> 4;
+        const double *src[CPT];
+        int E[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            src[c] = G + (size_t)block_col(P, Q, a.b, cg * CPT + c) * a.ldg + row0 + 2 * rp;
+            E[c] = cexp[cg * CPT + c];
+        }
+        double2 x[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) x[c] = *reinterpret_cast<const double2 *>(src[c]);
+        for (int t = 0; t < nsub; ++t) {
+            const int buf = t & 1;
+            if (t >= 2) bar_sync_buf<nb::kEmpty0, NT>(buf);
+            uint16_t *dst = Dg + (size_t)buf * split::kSlices * S::kGSlice + (cg * CPT) * S::kGLd + 2 * rp;
+            // column by column: digits of this sub-chunk, then the next
+            // sub-chunk's entries of the column are requested
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const unsigned long long z0 = split::fixed_biased(x[c].x, 0, E[c]);
+                const unsigned long long z1 = split::fixed_biased(x[c].y, 0, E[c]);
+                if (t + 1 < nsub) x[c] = *reinterpret_cast<const double2 *>(src[c] + (size_t)(t + 1) * S::kSub);
+#define JSVD_G2(I)                                                                                  \
+    *reinterpret_cast<uint32_t *>(dst + (I) * S::kGSlice + c * S::kGLd) =                           \
+        split::pack2(split::digit_bf16<I>(z0), split::digit_bf16<I>(z1));
+                JSVD_G2(0) JSVD_G2(1) JSVD_G2(2) JSVD_G2(3) JSVD_G2(4) JSVD_G2(5) JSVD_G2(6) JSVD_G2(7) JSVD_G2(8)
+#undef JSVD_G2
+            }
+            bar_arrive_buf<nb::kFull0, NT>(buf);
+        }
+    } else {
+        // ---------------- consumers ----------------
+        const int w = (threadIdx.x - NP) >> 5;
+        const int lane = threadIdx.x & 31;
+        const int t_ = w % S::kTiles, kpart = w / S::kTiles;
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= t_) ++I;
+        const int J = t_ - I * (I + 1) / 2;
+        float lev[split::kLevels][8];
+        split::zero_levels(lev);
+        for (int t = 0; t < nsub; ++t) {
+            const int buf = t & 1;
+            const int sub = t % S::kSubsPerChunk;
+            bar_sync_buf<nb::kFull0, NT>(buf);
+            if (sub % S::kKsplit == kpart) {
+                const uint16_t *D = Dg + (size_t)buf * split::kSlices * S::kGSlice;
+                split::tile_levels<S::kSub / 16>(D + I * 16 * S::kGLd, S::kGLd, S::kGSlice, D + J * 16 * S::kGLd,
+                                                 S::kGLd, S::kGSlice, lev);
+            }
+            if (t + 2 < nsub) bar_arrive_buf<nb::kEmpty0, NT>(buf);
+            if (sub == S::kSubsPerChunk - 1) {
+                if constexpr (S::kKsplit > 1) {
+                    // the K parts' level sums are exact integers: add them in part order
+                    if (kpart > 0) {
+                        float *mine = red + (((size_t)(kpart - 1) * S::kTiles + t_) * split::kLevels * 8) * 32 + lane;
+#pragma unroll
+                        for (int L = 0; L < split::kLevels; ++L)
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) mine[(L * 8 + e) * 32] = lev[L][e];
+                    }
+                    bar_sync<nb::kCons, NC>();
+                    if (kpart == 0) {
+                        for (int q = 1; q < S::kKsplit; ++q) {
+                            const float *src2 = red + (((size_t)(q - 1) * S::kTiles + t_) * split::kLevels * 8) * 32 + lane;
+#pragma unroll
+                            for (int L = 0; L < split::kLevels; ++L)
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) lev[L][e] += src2[(L * 8 + e) * 32];
+                        }
+                    }
+                    bar_sync<nb::kCons, NC>();
+                }
+                if (kpart == 0) {
+                    const int chunk = chunk0 + t / S::kSubsPerChunk;
+                    double *out = a.part + ((size_t)pair * a.g_chunks + chunk) * Cfg<BB>::kPacked;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int row = I * 16 + split::acc_row(e), col = J * 16 + split::acc_col(e);
+                        if (row < col) continue;
+                        float lv[split::kLevels];
+#pragma unroll
+                        for (int L = 0; L < split::kLevels; ++L) lv[L] = lev[L][e];
+                        out[packed_lower<BB>(row, col)] = split::combine<false>(lv, cexp[row], cexp[col]);
+                    }
+                }
+                split::zero_levels(lev);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// [X_P X_Q] := [X_P X_Q] V' on split digits, grid (units, pairs); a unit is
+// kUpdRowsPerCta rows of G (blockIdx.x < g_units) or of V.  For G the A
+// operand is G D^-1 (D from the pair's Gram diagonal) against the digits of
+// D V'; for V it is V against those of V'.  Row r of a block gets the exponent
+// bound E_r of its BB entries; X(r, k) = 2^(E_r + F_k - 40) * combine(levels).
+//
+// Warps 0-3 produce: load block t (thread p: row p % kMB, columns
+// 8 (p / kMB) .. +7), reduce the row exponents, write the digits to buffer
+// t % 2, and arrive on FULL(t % 2).  Warps 4-7 consume: wait on FULL, run the
+// level MMAs of their tile, read the tile rows' exponents, arrive on EMPTY
+// (which the producers wait on before refilling that buffer two blocks
+// later), then combine and store.  Named barriers with matched counts: every
+// producer and consumer thread runs the same number of blocks.
 template <int BB>
 __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PStepArgs a, int g_units) {
     using S = SplitCfg<BB>;
@@ -259,6 +347,10 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
         const int tm = cw / TN, tn = cw % TN;
         int gcol[8];
         int fx[8];
+        // exponent bounds of the written values per column (G only): columns
+        // of accumulators e = 0, 1, 4, 5
+        const bool track = ver == 0 && a.gexp != nullptr;
+        int cm[4] = {split::kNoExp, split::kNoExp, split::kNoExp, split::kNoExp};
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int col = tn * 16 + split::acc_col(e);
@@ -283,7 +375,25 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
 #pragma unroll
                 for (int L = 0; L < split::kLevels; ++L) lv[L] = lev[L][e];
                 const int row = (e & 2) ? r1 : r0;
-                X[(size_t)gcol[e] * ld + rb + row] = split::combine<true>(lv, (e & 2) ? e1 : e0, fx[e]);
+                const double y = split::combine<true>(lv, (e & 2) ? e1 : e0, fx[e]);
+                X[(size_t)gcol[e] * ld + rb + row] = y;
+                if (track) {
+                    const int ci = (e & 1) + ((e & 4) >> 1);
+                    cm[ci] = max(cm[ci], split::exp_bound(y, 0));
+                }
+            }
+        }
+        if (track) {
+            // lanes with the same lane % 4 hold the same columns
+#pragma unroll
+            for (int ci = 0; ci < 4; ++ci)
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) cm[ci] = max(cm[ci], __shfl_xor_sync(0xffffffffu, cm[ci], o));
+            if ((threadIdx.x & 31) < 4) {
+                atomicMax(&a.gexp[gcol[0]], cm[0]);
+                atomicMax(&a.gexp[gcol[1]], cm[1]);
+                atomicMax(&a.gexp[gcol[4]], cm[2]);
+                atomicMax(&a.gexp[gcol[5]], cm[3]);
             }
         }
     }
@@ -306,7 +416,8 @@ static void launch_split_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
     using S = SplitCfg<BB>;
     configure_split_once<BB>();
     if (ph == Phase::Gram) {
-        gram_split<BB><<<dim3(a.g_chunks, a.npairs), 32 * S::kGramWarps, gram_split_smem<BB>(), s>>>(a);
+        const int ctas = (a.g_chunks + S::kChunksPerCta - 1) / S::kChunksPerCta;
+        gram_split<BB><<<dim3(ctas, a.npairs), S::kGThreads, gram_split_smem<BB>(), s>>>(a);
         return;
     }
     const int gu = (ph == Phase::UpdateV) ? 0 : (a.g_rows + S::kUpdRowsPerCta - 1) / S::kUpdRowsPerCta;
