@@ -400,12 +400,17 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
     const int ring = side_streams ? kVRing : 1;
     if ((rc = ensure(vprime, sizeof(double) * (size_t)npairs * BB * BB * ring))) return rc;
     if ((rc = ensure(vflag, sizeof(int) * (size_t)npairs * ring))) return rc;
+    // Split contractions update V in the same launch as G (one slot): their
+    // issue-heavy update CTAs slowed the latency-bound Jacobi kernel by more
+    // than the overlap gained (measured on every workload but the 8192^2 one,
+    // where the two were within 2 %).  The FP64 FMA form overlaps the V update
+    // on the side stream.
     const bool split = o.contraction == JSVD_CONTRACT_SPLIT;
-    const size_t bsl_pairs = (size_t)npairs * 2 * (size_t)split_b_elems_rt(BB);   // per ring slot
+    const size_t bsl_pairs = (size_t)npairs * 2 * (size_t)split_b_elems_rt(BB);
     if (split) {
-        if ((rc = ensure(bslice, sizeof(uint16_t) * bsl_pairs * ring))) return rc;
-        if ((rc = ensure(bexp, sizeof(int) * (size_t)npairs * 2 * BB * ring))) return rc;
-        if ((rc = ensure(dexp, sizeof(int) * (size_t)npairs * BB * ring))) return rc;
+        if ((rc = ensure(bslice, sizeof(uint16_t) * bsl_pairs))) return rc;
+        if ((rc = ensure(bexp, sizeof(int) * (size_t)npairs * 2 * BB))) return rc;
+        if ((rc = ensure(dexp, sizeof(int) * (size_t)npairs * BB))) return rc;
         if ((rc = ensure(gexp, sizeof(int) * (size_t)n_pad))) return rc;
     }
     if (side_streams && (rc = ensure_side_stream())) return rc;
@@ -471,11 +476,12 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         *conv = 0;
         while (*done < limit) {
             cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
-            const bool side = side_streams && a.V != nullptr;
+            const bool side = side_streams && a.V != nullptr && !a.split;
+            const int nslot = side ? ring : 1;
             for (int s = 0; s < nb - 1; ++s) {
                 // V' and its flags rotate through a ring of slots so that the V
                 // update of step s can still read its slot while steps s+1.. run
-                const int slot = s % ring;
+                const int slot = s % nslot;
                 a.step = s;
                 a.vprime = (double *)vprime.ptr + (size_t)slot * npairs * BB * BB;
                 a.vflag = (int *)vflag.ptr + (size_t)slot * npairs;
