@@ -42,6 +42,13 @@ FP64_FLOP_PER_CYCLE = 152 * 4 * 32 * 2 // 64
 # traffic grows in proportion to the units, so a launch's traffic is this
 # figure times its units (algorithmic: 1024 B per unit, read + write).
 UPDATE_BYTES_PER_PAIR_ROW = 477.94e6 / (64 * 8192)
+# The same figure for update_split<64> (the tensor-core update, G and V in one
+# launch): ncu, 4096x4096 graded, b = 32, every pair updated, 279.6 MB read +
+# 212.9 MB written for 2 x 64 pairs x 4096 rows.
+SPLIT_UPDATE_BYTES_PER_PAIR_ROW = 492.508e6 / (2 * 64 * 4096)
+# bf16 digit products per FP64 product in the split contractions (9 slices,
+# levels i + l <= 8)
+SPLIT_PRODUCTS = 45
 
 WORKLOADS = {
     # name: (m, n, generator, description)
@@ -67,6 +74,17 @@ def fp64_peak_tflops(sustained: bool) -> tuple[float, str]:
     except Exception:
         fb = 1700.0 if sustained else 1900.0
         return fb * NOMINAL_FP64_TF / NOMINAL_BF16_TF, "fallback bf16 x nominal FP64/bf16 ratio"
+
+
+def bf16_peak_tflops(sustained: bool) -> tuple[float, str]:
+    """Measured dense bf16 tensor peak of the GB300s."""
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    try:
+        pk = json.load(open(PEAKS_FILE))
+        return float(pk[key]), f"MEASURED_PEAKS.json {key} = {pk[key]} TF/s"
+    except Exception:
+        fb = 1700.0 if sustained else 1900.0
+        return fb, f"fallback bf16 {'sustained' if sustained else 'burst'} {fb} TF/s"
 
 
 def make_input(name: str, seed: int) -> np.ndarray:
@@ -307,6 +325,7 @@ def run_gpu(args) -> None:
 
     # FP64 peak of this GPU, measured now (warm clocks), for the roofline
     peak_dfma, peak_dmma = J.fp64_peak(seconds=args.peak_seconds)
+    peak_mma = J.bf16_mma_peak(seconds=args.peak_seconds) if args.contraction == "split" else None
     torch.cuda.synchronize()
 
     # ---- timed region: K complete SVDs with inputs resident in HBM ------------
@@ -376,24 +395,47 @@ def run_gpu(args) -> None:
     peak = FP64_FLOP_PER_CYCLE * sm_mhz * 1e6 / 1e12
     achieved = d_flops / (d_ms * 1e-3) / 1e12 if d_ms > 0 else 0.0
     traffic = None
-    if dom == "update" and d_launch:
-        # ncu: 912 B of DRAM traffic per (pair, row) of block_update<64, double>
-        bb = 2 * last_b
-        traffic = UPDATE_BYTES_PER_PAIR_ROW * (d_flops / (2.0 * bb * bb)) / d_launch
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": traffic,
-                "kernel": {"gram": "gram_partial", "jacobi": "pair_jacobi", "update": "block_update"}[dom],
-                "launches": d_launch,
-                "peak_source": (f"FP64 pipe: {FP64_FLOP_PER_CYCLE} flop/cycle (152 SMs x 4 sub-partitions x one "
-                                f"DFMA warp instruction per 64 cycles, the sm__inst_executed_pipe_fp64 peak) x "
-                                f"median SM clock {sm_mhz:.0f} MHz in the timed region; in-run probes: DMMA "
-                                f"{peak_dmma:.3f}, DFMA {peak_dfma:.3f} TFLOP/s"),
-                "peak_derived": {"value": derived, "source": derived_src}}
+    bb = 2 * last_b
+    per_row = SPLIT_UPDATE_BYTES_PER_PAIR_ROW if args.contraction == "split" else UPDATE_BYTES_PER_PAIR_ROW
+    if dom == "update" and d_launch and per_row is not None:
+        # ncu DRAM bytes per (pair, row) of the update kernel x the launch's units
+        traffic = per_row * (d_flops / (2.0 * bb * bb)) / d_launch
+    fp64_src = (f"FP64 pipe: {FP64_FLOP_PER_CYCLE} flop/cycle (152 SMs x 4 sub-partitions x one DFMA warp "
+                f"instruction per 64 cycles, the sm__inst_executed_pipe_fp64 peak) x median SM clock "
+                f"{sm_mhz:.0f} MHz in the timed region; in-run probes: DMMA {peak_dmma:.3f}, DFMA "
+                f"{peak_dfma:.3f} TFLOP/s")
+    if args.contraction == "split" and dom in ("gram", "update"):
+        # tensor-core kernels: each FP64 product is SPLIT_PRODUCTS bf16 digit products
+        bf16_peak, bf16_src = bf16_peak_tflops(sustained=True)
+        tensor = SPLIT_PRODUCTS * achieved
+        roofline = {"bound": "tensor", "achieved": tensor, "peak": bf16_peak, "unit": "TFLOP/s",
+                    "frac": tensor / bf16_peak, "traffic": traffic,
+                    "kernel": {"gram": "gram_split", "update": "update_split"}[dom], "launches": d_launch,
+                    "peak_source": bf16_src + " (of measured); achieved = "
+                                   f"{SPLIT_PRODUCTS} bf16 digit products x the kernel's algorithmic FP64 flops / "
+                                   "its CUDA-event time",
+                    "fp64_equivalent_tflops": achieved,
+                    "mma_sync_bf16_peak": peak_mma,
+                    "frac_of_mma_sync_peak": tensor / peak_mma if peak_mma else None}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak if peak else None, "traffic": traffic,
+                    "kernel": {"gram": "gram_partial", "jacobi": "pair_jacobi", "update": "block_update"}[dom],
+                    "launches": d_launch, "peak_source": fp64_src,
+                    "peak_derived": {"value": derived, "source": derived_src}}
     kernels = {c: {"ms": prof[c][0], "launches": prof[c][1], "tflops": (prof[c][2] / (prof[c][0] * 1e-3) / 1e12)
                    if prof[c][0] > 0 else None, "share": prof[c][0] / ms_total if ms_total else None}
                for c in ("gram", "jacobi", "update", "update_v")}
-    kernels["update_v"]["note"] = ("V update on the low-priority side stream: it runs in the main stream's gaps, "
-                                   "so its event time includes waiting for SMs and overlaps the other classes")
+    if args.contraction == "split":
+        kernels["update"]["note"] = "update of G and V in one launch (tensor-core split contractions)"
+        for c in ("gram", "update"):
+            if kernels[c]["tflops"]:
+                kernels[c]["tensor_tflops"] = SPLIT_PRODUCTS * kernels[c]["tflops"]
+        kernels["update_v"]["note"] = "no side-stream V update with split contractions"
+    else:
+        kernels["update_v"]["note"] = ("V update on the low-priority side stream: it runs in the main stream's "
+                                       "gaps, so its event time includes waiting for SMs and overlaps the other "
+                                       "classes")
 
     cpu = None
     mixed_report = None
