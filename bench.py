@@ -529,10 +529,10 @@ def main():
                    help="sweep count the reference arm scales its sample by")
     args = p.parse_args()
     if args.b is None and args.workload != "batched4096":
-        # block widths chosen by timing b in {16, 32} on this GPU: 32 for the
-        # graded 8192^2 and mixed workloads, 16 for the 4096^2 HSVD (only 64 pivot
-        # pairs per p-step at b = 32, so its latency-bound Jacobi phase dominates)
-        args.b = 16 if WORKLOADS[args.workload][2] == "hsvd" or args.workload == "small512" else 32
+        # block widths chosen by timing b in {8, 16, 32} on this GPU (split
+        # contractions): 32 for the graded 8192^2, HSVD 4096^2 and mixed
+        # workloads; 16 for the 512 x 256 one (the width its configuration names)
+        args.b = 16 if args.workload == "small512" else 32
     if args.strategy is None:
         args.strategy = "modulus" if args.workload == "small512" else "rR"
     if args.impl == "reference":

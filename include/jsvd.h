@@ -226,6 +226,13 @@ int jsvd_profile_read(jsvd_ctx_t ctx, double *ms, long long *launches, double *f
  * pointer may be NULL.  Allocates and frees a small scratch buffer.        */
 int jsvd_fp64_peak(jsvd_ctx_t ctx, double seconds, double *dfma_tflops, double *dmma_tflops);
 
+/* Measured throughput of the bf16 tensor-core instruction the split
+ * contractions issue (mma.sync m16n8k16, FP32 accumulation), all SMs busy for
+ * about `seconds` (0 < seconds <= 60) after an equal warm-up: the ceiling of
+ * those kernels' roofline.  Not part of the paper.  Returns 0, or -1 (null
+ * ctx), -2 (seconds out of range), JSVD_ERR_CUDA. */
+int jsvd_bf16_mma_peak(jsvd_ctx_t ctx, double seconds, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,7 +59,7 @@ _ctx: dict[int, ctypes.c_void_p] = {}
 EXPORTED = ["jsvd_default_opts", "jsvd_create", "jsvd_destroy", "jsvd_set_stream",
             "jsvd_last_error", "jsvd_status_string", "jsvd_dgesvj", "jsvd_dhsvj",
             "jsvd_pivot_table", "jsvd_rotation_params", "jsvd_profile", "jsvd_profile_read",
-            "jsvd_fp64_peak", "jsvd_dgesvj_batched", "jsvd_dgesvj_backward",
+            "jsvd_fp64_peak", "jsvd_bf16_mma_peak", "jsvd_dgesvj_batched", "jsvd_dgesvj_backward",
             "jsvd_dgesvj_noalloc"]
 
 
@@ -88,6 +88,7 @@ def library():
             lib.jsvd_profile.argtypes = [P, I]
             lib.jsvd_profile_read.argtypes = [P, P, P, P, I]
             lib.jsvd_fp64_peak.argtypes = [P, D, P, P]
+            lib.jsvd_bf16_mma_peak.argtypes = [P, D, P]
             lib.jsvd_dgesvj_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P,
                                                 ctypes.POINTER(Opts), P]
             lib.jsvd_dgesvj_backward.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P, P, P]
@@ -244,6 +245,16 @@ def fp64_peak(seconds: float = 1.0, device: int | None = None) -> tuple[float, f
     if rc:
         _raise(rc, h)
     return a.value, b.value
+
+
+def bf16_mma_peak(seconds: float = 1.0, device: int | None = None) -> float:
+    """bf16 mma.sync (m16n8k16) TFLOP/s of this GPU measured by the library's probe."""
+    a = ctypes.c_double()
+    h = context(device)
+    rc = library().jsvd_bf16_mma_peak(h, float(seconds), ctypes.byref(a))
+    if rc:
+        _raise(rc, h)
+    return a.value
 
 
 # ---------------------------------------------------------------------------
