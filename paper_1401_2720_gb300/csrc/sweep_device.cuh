@@ -155,20 +155,20 @@ __device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int 
 // memory (column-major, ld BB+1).  Column k of a version gets the exponent
 // bound F_k of its entries and the digits of trunc(x 2^(62-F_k)), stored as
 // out[slice][k][j] (K = j contiguous, row stride BB + kPad).
-template <int BB>
+template <int BB, int NT = Cfg<BB>::kJacThreads>
 __device__ __forceinline__ void split_right_factor(const double *W, const double *hdiag, int *dx,
                                                    uint16_t *__restrict__ out, int *__restrict__ bexp,
                                                    int *__restrict__ dexp) {
     using C = Cfg<BB>;
     constexpr int LD = BB + split::kPad;
-    for (int j = threadIdx.x; j < BB; j += C::kJacThreads) {
+    for (int j = threadIdx.x; j < BB; j += NT) {
         const double h = hdiag[j];
         const int d = h > 0.0 ? (split::exp_of(h) >> 1) : 0;
         dx[j] = d;
         dexp[j] = d;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * BB; t += C::kJacThreads) {
+    for (int t = threadIdx.x; t < 2 * BB; t += NT) {
         const int ver = t / BB, k = t % BB;
         const double *w = W + k * C::kLd;
         int F = split::kNoExp;
@@ -185,6 +185,141 @@ __device__ __forceinline__ void split_right_factor(const double *W, const double
             JSVD_SPLIT_STORE(0) JSVD_SPLIT_STORE(1) JSVD_SPLIT_STORE(2) JSVD_SPLIT_STORE(3) JSVD_SPLIT_STORE(4)
             JSVD_SPLIT_STORE(5) JSVD_SPLIT_STORE(6) JSVD_SPLIT_STORE(7) JSVD_SPLIT_STORE(8)
 #undef JSVD_SPLIT_STORE
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One inner sweep (block-oriented variant) with 2 kJacThreads threads: the
+// first half (R side) forms each inner p-step's dot products on R, the
+// relative test, the rotations (Eqs. (4.3)-(4.6)) and the P2 sort decision,
+// publishes them in one of two parameter slots and rotates R; the second half
+// (V' side) rotates V' with the published parameters one step behind (V'
+// does not feed the next dot products).  Both halves do each element's
+// arithmetic exactly as the single-group sweep does, so R and V' are the
+// same bit for bit; the V' side's FP64 work fills the FP64 pipe while the R
+// side waits on its latency chains.  Named barriers: FULL (slot filled,
+// R side arrives, V' side waits), EMPTY (slot read, V' side arrives, R side
+// waits before refilling it two steps later), one per side per step.
+namespace jb {
+constexpr int kFull0 = 1, kEmpty0 = 3, kRSide = 5, kVSide = 6;
+}
+template <int ID, int COUNT>
+__device__ __forceinline__ void nbar_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
+}
+template <int ID, int COUNT>
+__device__ __forceinline__ void nbar_arrive() {
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
+}
+
+template <int BB>
+__device__ __forceinline__ void jacobi_sweep_pipelined(double *A, double *B, const unsigned char *tab, int P, int Q,
+                                                       int b, int nplus, int bord_lo, int bord_hi, double c_eps,
+                                                       int &my_rot, int &my_proper, int &changed) {
+    using C = Cfg<BB>;
+    constexpr int NH = C::kJacThreads;        // threads per side
+    constexpr int NT = 2 * NH;
+    constexpr int NP = BB / 2;                // pairs per inner step
+    __shared__ double s_cs[2][NP], s_tn[2][NP];
+    __shared__ int s_fl[2][NP];               // bit 0: rotate, bit 1: swap, bit 2: hyperbolic
+    const int tid = threadIdx.x;
+    if (tid < NH) {
+        // ---------------- R side ----------------
+        const int y = tid / C::kLanesPerPair;
+        const int g = tid % C::kLanesPerPair;
+        for (int st = 0; st < BB - 1; ++st) {
+            const int slot = st & 1;
+            const int p = tab[2 * (st * (BB / 2) + y)];
+            const int q = tab[2 * (st * (BB / 2) + y) + 1];
+            double *rp = B + p * C::kLd, *rq = B + q * C::kLd;
+            double hpp = 0.0, hqq = 0.0, hpq = 0.0;
+#pragma unroll
+            for (int k = 0; k < C::kRowsPerLane; ++k) {
+                const int r = g + k * C::kLanesPerPair;
+                const double x = rp[r], z = rq[r];
+                hpp = __fma_rn(x, x, hpp);
+                hqq = __fma_rn(z, z, hqq);
+                hpq = __fma_rn(x, z, hpq);
+            }
+#pragma unroll
+            for (int off = C::kLanesPerPair / 2; off > 0; off >>= 1) {
+                hpp = __dadd_rn(hpp, __shfl_xor_sync(0xffffffffu, hpp, off));
+                hqq = __dadd_rn(hqq, __shfl_xor_sync(0xffffffffu, hqq, off));
+                hpq = __dadd_rn(hpq, __shfl_xor_sync(0xffffffffu, hpq, off));
+            }
+            const int gp = block_col(P, Q, b, p), gq = block_col(P, Q, b, q);
+            const bool hyp = gp < nplus && gq >= nplus;
+            const bool border = (gp >= bord_lo && gp < bord_hi) || (gq >= bord_lo && gq < bord_hi);
+            const bool rho = !border && needs_rotation(hpp, hqq, hpq, c_eps);
+            Rot rot{1.0, 0.0};
+            if (rho) rot = rot_params(hpp, hqq, hpq, hyp);
+            bool swap = false;
+            if (!hyp && !border) {
+                const double npp = rho ? __fma_rn(-rot.tn, hpq, hpp) : hpp;
+                const double nqq = rho ? __fma_rn(rot.tn, hpq, hqq) : hqq;
+                swap = (gq < nplus && npp < nqq) || (gp >= nplus && npp > nqq);
+            }
+            if (st >= 2) {
+                if (slot) nbar_sync<jb::kEmpty0 + 1, NT>(); else nbar_sync<jb::kEmpty0, NT>();
+            }
+            if (g == 0) {
+                s_cs[slot][y] = rot.cs;
+                s_tn[slot][y] = rot.tn;
+                s_fl[slot][y] = (rho ? 1 : 0) | (swap ? 2 : 0) | (hyp ? 4 : 0);
+            }
+            if (slot) nbar_arrive<jb::kFull0 + 1, NT>(); else nbar_arrive<jb::kFull0, NT>();
+            if (rho || swap) {
+#pragma unroll
+                for (int k = 0; k < C::kRowsPerLane; ++k) {
+                    const int r = g + k * C::kLanesPerPair;
+                    double x = rp[r], z = rq[r];
+                    if (rho) rot_apply(x, z, hyp, rot);
+                    if (swap) {
+                        rp[r] = z; rq[r] = x;
+                    } else {
+                        rp[r] = x; rq[r] = z;
+                    }
+                }
+                changed = 1;
+            }
+            if (g == 0 && rho) {
+                ++my_rot;
+                if (is_proper(rot)) ++my_proper;
+            }
+            nbar_sync<jb::kRSide, NH>();
+        }
+    } else {
+        // ---------------- V' side ----------------
+        const int v = tid - NH;
+        const int y = v / C::kLanesPerPair;
+        const int g = v % C::kLanesPerPair;
+        for (int st = 0; st < BB - 1; ++st) {
+            const int slot = st & 1;
+            const int p = tab[2 * (st * (BB / 2) + y)];
+            const int q = tab[2 * (st * (BB / 2) + y) + 1];
+            if (slot) nbar_sync<jb::kFull0 + 1, NT>(); else nbar_sync<jb::kFull0, NT>();
+            const Rot rot{s_cs[slot][y], s_tn[slot][y]};
+            const int fl = s_fl[slot][y];
+            if (st + 2 < BB - 1) {
+                if (slot) nbar_arrive<jb::kEmpty0 + 1, NT>(); else nbar_arrive<jb::kEmpty0, NT>();
+            }
+            const bool rho = fl & 1, swap = fl & 2, hyp = fl & 4;
+            double *wp = A + p * C::kLd, *wq = A + q * C::kLd;
+            if (rho || swap) {
+#pragma unroll
+                for (int k = 0; k < C::kRowsPerLane; ++k) {
+                    const int r = g + k * C::kLanesPerPair;
+                    double u = wp[r], w = wq[r];
+                    if (rho) rot_apply(u, w, hyp, rot);
+                    if (swap) {
+                        wp[r] = w; wq[r] = u;
+                    } else {
+                        wp[r] = u; wq[r] = w;
+                    }
+                }
+            }
+            nbar_sync<jb::kVSide, NH>();
         }
     }
 }
@@ -207,7 +342,7 @@ __device__ __forceinline__ void split_right_factor(const double *W, const double
 // of the pair's columns of G are reset (the split update recomputes them).  Global columns in [bord_lo, bord_hi) are the
 // identity border: they are exactly orthogonal to everything, and they are
 // neither rotated nor swapped, so they keep their positions.
-template <int BB>
+template <int BB, int NT = Cfg<BB>::kJacThreads>
 __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int chunks,
                                             const unsigned char *__restrict__ inner, int P, int Q, int b,
                                             int nplus, int bord_lo, int bord_hi, int inner_sweeps, double eps,
@@ -228,13 +363,13 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     __shared__ int s_cnt[2];
 
     const int tid = threadIdx.x;
-    for (int e = tid; e < (BB - 1) * BB; e += C::kJacThreads) tab[e] = inner[e];
+    for (int e = tid; e < (BB - 1) * BB; e += NT) tab[e] = inner[e];
     if (tid == 0) { s_off = 0ull; s_brk = 0; s_cnt[0] = 0; s_cnt[1] = 0; }
 
     // (1) H = sum of the row-chunk partials in a fixed order: chunk c goes to
     // accumulator c mod 8 (in increasing c), then the 8 accumulators are added
     // pairwise; short dependency chains keep the FP64 latency off the path
-    for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+    for (int e = tid; e < BB * BB; e += NT) {
         const int i = e % BB, j = e / BB;
         if (i < j) continue;
         const int k = packed_lower<BB>(i, j);
@@ -254,7 +389,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
 
     // (2) normalized off-diagonal maximum of H, max |h_ij| / sqrt(h_ii h_jj)
     // (reported only): B[j] = 1/sqrt(h_jj) first, then two products per entry
-    for (int j = tid; j < BB; j += C::kJacThreads) {
+    for (int j = tid; j < BB; j += NT) {
         const double d = A[j + j * C::kLd];
         B[j] = d > 0.0 ? rsqrt(d) : 0.0;
         hdiag[j] = d;
@@ -262,7 +397,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     __syncthreads();
     {
         double mx = 0.0;
-        for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+        for (int e = tid; e < BB * BB; e += NT) {
             const int i = e % BB, j = e / BB;
             if (i <= j) continue;
             mx = fmax(mx, fabs(A[i + j * C::kLd]) * B[i] * B[j]);
@@ -285,11 +420,11 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
         }
         __syncthreads();
         const double piv = s_piv;
-        for (int i = k + tid; i < BB; i += C::kJacThreads)
+        for (int i = k + tid; i < BB; i += NT)
             A[i + k * C::kLd] = (piv > 0.0) ? (i == k ? piv : __ddiv_rn(A[i + k * C::kLd], piv)) : 0.0;
         __syncthreads();
         const int rem = BB - 1 - k;
-        for (int e = tid; e < rem * rem; e += C::kJacThreads) {
+        for (int e = tid; e < rem * rem; e += NT) {
             const int i = k + 1 + e % rem, j = k + 1 + e / rem;
             if (i >= j)
                 A[i + j * C::kLd] = __fma_rn(-A[i + k * C::kLd], A[j + k * C::kLd], A[i + j * C::kLd]);
@@ -298,22 +433,29 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     }
 
     // (4) R = L^T into B; V' = I into A
-    for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+    for (int e = tid; e < BB * BB; e += NT) {
         const int i = e % BB, j = e / BB;
         B[i + j * C::kLd] = (i <= j) ? A[j + i * C::kLd] : 0.0;
     }
     __syncthreads();
-    for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+    for (int e = tid; e < BB * BB; e += NT) {
         const int i = e % BB, j = e / BB;
         A[i + j * C::kLd] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
 
     // (5) inner sweeps of the pointwise one-sided method on R (Sec. 4.3)
-    const int y = tid / C::kLanesPerPair;
-    const int g = tid % C::kLanesPerPair;
     const double c_eps = eps * sqrt((double)BB);   // c(eps) = eps sqrt(nhat), nhat = BB
     int my_rot = 0, my_proper = 0, changed = 0, sweeps_done = 0;
+    if constexpr (NT == 2 * C::kJacThreads) {
+        // one inner sweep, V' rotated one step behind R by the second half of
+        // the threads
+        jacobi_sweep_pipelined<BB>(A, B, tab, P, Q, b, nplus, bord_lo, bord_hi, c_eps, my_rot, my_proper, changed);
+        sweeps_done = 1;
+    } else {
+    static_assert(NT == C::kJacThreads, "thread count");
+    const int y = tid / C::kLanesPerPair;
+    const int g = tid % C::kLanesPerPair;
     for (int sw = 0; sw < inner_sweeps; ++sw) {
         int sweep_rot = 0;
         ++sweeps_done;
@@ -373,17 +515,18 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
         }
         if (inner_sweeps > 1 && __syncthreads_count(sweep_rot) == 0) break;
     }
+    }
 
     // (6) V' and its flag to global memory; counters
     const int any_change = __syncthreads_or(changed);
-    for (int e = tid; e < BB * BB; e += C::kJacThreads) {
+    for (int e = tid; e < BB * BB; e += NT) {
         const int i = e % BB, j = e / BB;
         vp[e] = A[i + j * C::kLd];
     }
-    if (bsl && any_change) split_right_factor<BB>(A, hdiag, dx, bsl, bexp, dexp);
+    if (bsl && any_change) split_right_factor<BB, NT>(A, hdiag, dx, bsl, bexp, dexp);
     // the update of G rewrites these columns and max-reduces their new bounds
     if (gexp && any_change)
-        for (int k = tid; k < BB; k += C::kJacThreads) gexp[block_col(P, Q, b, k)] = split::kNoExp;
+        for (int k = tid; k < BB; k += NT) gexp[block_col(P, Q, b, k)] = split::kNoExp;
     atomicAdd(&s_cnt[0], my_rot);
     atomicAdd(&s_cnt[1], my_proper);
     __syncthreads();
