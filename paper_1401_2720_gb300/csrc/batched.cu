@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(Cfg<BB>::kGramThreads) kb_gram(BArgs a, int of
                           a.part + M.part_off + ((size_t)pair * M.g_chunks + chunk) * Cfg<BB>::kPacked, smem);
 }
 
-template <int BB>
-__global__ void __launch_bounds__(Cfg<BB>::kJacThreads) kb_jacobi(BArgs a, int off, int count, int step) {
+// NT = 2 kJacThreads (one inner sweep): V' rotated by a second thread group.
+template <int BB, int NT>
+__global__ void __launch_bounds__(NT) kb_jacobi(BArgs a, int off, int count, int step) {
     extern __shared__ __align__(16) double smem[];
     const BUnit u = a.units[off + find_unit(a.units + off, count, blockIdx.x)];
     const BMat M = a.mats[u.mat];
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(Cfg<BB>::kJacThreads) kb_jacobi(BArgs a, int o
     const int pair = blockIdx.x - u.start;
     const int P = a.tables[M.tab_off + 2 * (step * M.npairs + pair)];
     const int Q = a.tables[M.tab_off + 2 * (step * M.npairs + pair) + 1];
-    jacobi_unit<BB>(a.part + M.part_off + (size_t)pair * M.g_chunks * Cfg<BB>::kPacked, M.g_chunks, a.inner, P,
+    jacobi_unit<BB, NT>(a.part + M.part_off + (size_t)pair * M.g_chunks * Cfg<BB>::kPacked, M.g_chunks, a.inner, P,
                     Q, M.b, M.n_pad, M.n, M.n_pad, a.inner_sweeps, kEps, a.vprime + M.vp_off + (size_t)pair * BB * BB,
                     a.vflag + M.vflag_off + pair, a.counters + (size_t)u.mat * kCntSize, smem);
 }
@@ -464,9 +465,15 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
     cudaFuncSetAttribute(kb_gram<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem_bytes<16, double>());
     cudaFuncSetAttribute(kb_gram<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem_bytes<32, double>());
     cudaFuncSetAttribute(kb_gram<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem_bytes<64, double>());
-    cudaFuncSetAttribute(kb_jacobi<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem_bytes<16>());
-    cudaFuncSetAttribute(kb_jacobi<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem_bytes<32>());
-    cudaFuncSetAttribute(kb_jacobi<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem_bytes<64>());
+#define JSVD_JAC_ATTR(BBV)                                                                              \
+    cudaFuncSetAttribute(kb_jacobi<BBV, Cfg<BBV>::kJacThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                         (int)jacobi_smem_bytes<BBV>());                                                 \
+    cudaFuncSetAttribute(kb_jacobi<BBV, 2 * Cfg<BBV>::kJacThreads>,                                      \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem_bytes<BBV>());
+    JSVD_JAC_ATTR(16)
+    JSVD_JAC_ATTR(32)
+    JSVD_JAC_ATTR(64)
+#undef JSVD_JAC_ATTR
     cudaFuncSetAttribute(kb_update<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem_bytes<16, double>());
     cudaFuncSetAttribute(kb_update<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem_bytes<32, double>());
     cudaFuncSetAttribute(kb_update<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem_bytes<64, double>());
@@ -541,9 +548,12 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         if (p.kind == 0)                                                                                \
             launch_prio(kb_gram<BBV>, units_n, Cfg<BBV>::kGramThreads, gram_smem_bytes<BBV, double>(), st, \
                         prio, a, off, cnt, p.step);                                                     \
+        else if (p.kind == 1 && ba.inner_sweeps == 1)                                                   \
+            launch_prio(kb_jacobi<BBV, 2 * Cfg<BBV>::kJacThreads>, units_n, 2 * Cfg<BBV>::kJacThreads,  \
+                        jacobi_smem_bytes<BBV>(), st, prio, a, off, cnt, p.step);                       \
         else if (p.kind == 1)                                                                           \
-            launch_prio(kb_jacobi<BBV>, units_n, Cfg<BBV>::kJacThreads, jacobi_smem_bytes<BBV>(), st,   \
-                        prio, a, off, cnt, p.step);                                                     \
+            launch_prio(kb_jacobi<BBV, Cfg<BBV>::kJacThreads>, units_n, Cfg<BBV>::kJacThreads,          \
+                        jacobi_smem_bytes<BBV>(), st, prio, a, off, cnt, p.step);                       \
         else                                                                                            \
             launch_prio(kb_update<BBV>, units_n, kUpdThreads, update_smem_bytes<BBV, double>(), st,     \
                         prio, a, off, cnt, p.step, p.kind - 2);                                         \
