@@ -128,16 +128,21 @@ __device__ __forceinline__ void tile_levels(const uint16_t *As, int a_ld, int a_
 #pragma unroll
         for (int l = 0; l < kSlices; ++l)
             ldsm_x4(b0 + 2u * (uint32_t)(l * b_slice + 16 * ks), bf[l][0], bf[l][1], bf[l][2], bf[l][3]);
+        // A digit fragments double-buffered: slice i + 1 is requested before the
+        // MMAs of slice i are issued
+        uint32_t af[2][4];
+        ldsm_x4(a0 + 2u * (uint32_t)(16 * ks), af[0][0], af[0][1], af[0][2], af[0][3]);
 #pragma unroll
         for (int i = 0; i < kSlices; ++i) {
-            uint32_t af[4];
-            ldsm_x4(a0 + 2u * (uint32_t)(i * a_slice + 16 * ks), af[0], af[1], af[2], af[3]);
+            if (i + 1 < kSlices)
+                ldsm_x4(a0 + 2u * (uint32_t)((i + 1) * a_slice + 16 * ks), af[(i + 1) & 1][0], af[(i + 1) & 1][1],
+                        af[(i + 1) & 1][2], af[(i + 1) & 1][3]);
 #pragma unroll
             for (int l = 0; l < kSlices - i; ++l) {
                 float(&d0)[4] = *reinterpret_cast<float(*)[4]>(&lev[i + l][0]);
                 float(&d1)[4] = *reinterpret_cast<float(*)[4]>(&lev[i + l][4]);
-                mma_bf16(d0, af, bf[l][0], bf[l][1]);
-                mma_bf16(d1, af, bf[l][2], bf[l][3]);
+                mma_bf16(d0, af[i & 1], bf[l][0], bf[l][1]);
+                mma_bf16(d1, af[i & 1], bf[l][2], bf[l][3]);
             }
         }
     }

@@ -28,17 +28,19 @@ template <int BB> struct SplitCfg {
     static constexpr int kGLd = kSub + split::kPad;                    // 40
     static constexpr int kGSlice = BB * kGLd;
     static constexpr int kCPT = BB / 4;                                // columns per producer thread
-    // update: 4 producer warps (load, exponents, digits) and 4 consumer warps
-    // (one 16x16 output tile each) over double-buffered blocks of kMB rows;
-    // every producer thread holds 8 entries of a block (one row, 8 columns)
-    static constexpr int kCG = BB / 8;                                 // column groups of 8
-    static constexpr int kMB = 128 / kCG;                              // rows per block: 16, 32, 64
+    // update: 4 producer warps (load, exponents, digits) and 8 consumer warps
+    // (one 16x16 output tile each, two per SM sub-partition) over
+    // double-buffered blocks of kMB rows; every producer thread holds 16
+    // entries of a block (one row, 16 columns)
+    static constexpr int kCG = BB / 16;                                // column groups of 16
+    static constexpr int kMB = 128 / kCG;                              // rows per block: 32, 64, 128
     static constexpr int kULd = BB + split::kPad;
     static constexpr int kUSliceA = kMB * kULd;
     static constexpr int kUSliceB = BB * kULd;
-    static constexpr int kUpdWarps = 8;
+    static constexpr int kUpdProd = 4, kUpdCons = 8;
+    static constexpr int kUpdWarps = kUpdProd + kUpdCons;
     static constexpr int kUpdRowsPerCta = 512;                         // rows of one update CTA
-    static_assert((kMB / 16) * (BB / 16) == 4, "one tile per consumer warp");
+    static_assert((kMB / 16) * (BB / 16) == kUpdCons, "one tile per consumer warp");
 };
 
 template <int BB>
@@ -252,10 +254,10 @@ __global__ void __launch_bounds__(SplitCfg<BB>::kGThreads, 1) gram_split(PStepAr
 // bound E_r of its BB entries; X(r, k) = 2^(E_r + F_k - 40) * combine(levels).
 //
 // Warps 0-3 produce: load block t (thread p: row p % kMB, columns
-// 8 (p / kMB) .. +7), reduce the row exponents, write the digits to buffer
-// t % 2, and arrive on FULL(t % 2).  Warps 4-7 consume: wait on FULL, run the
-// level MMAs of their tile, read the tile rows' exponents, arrive on EMPTY
-// (which the producers wait on before refilling that buffer two blocks
+// 16 (p / kMB) .. +15), reduce the row exponents, write the digits to buffer
+// t % 2, and arrive on FULL(t % 2).  Warps 4-11 consume: wait on FULL, run
+// the level MMAs of their tile, read the tile rows' exponents, arrive on
+// EMPTY (which the producers wait on before refilling that buffer two blocks
 // later), then combine and store.  Named barriers with matched counts: every
 // producer and consumer thread runs the same number of blocks.
 template <int BB>
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
     using S = SplitCfg<BB>;
     constexpr int MB = S::kMB;
     constexpr int CG = S::kCG;
-    constexpr int NT = 32 * S::kUpdWarps;             // 256
-    constexpr int NP = NT / 2;                         // producer threads
+    constexpr int NT = 32 * S::kUpdWarps;             // 384
+    constexpr int NP = 32 * S::kUpdProd;               // producer threads
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                 // [2][kSlices][MB][kULd]
     uint16_t *Bs = As + 2 * split::kSlices * S::kUSliceA;                   // [kSlices][BB][kULd]
@@ -302,47 +304,49 @@ __global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) update_split(PSt
         const int p = threadIdx.x;
         const int r = p % MB, cg = p / MB;
         const double *src0 = X + rbeg + r;
-        size_t coff[8];
-        int dx[8];
+        size_t coff[16];
+        int dx[16];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            coff[c] = (size_t)block_col(P, Q, a.b, 8 * cg + c) * ld;
-            dx[c] = dexp[8 * cg + c];
+        for (int c = 0; c < 16; ++c) {
+            coff[c] = (size_t)block_col(P, Q, a.b, 16 * cg + c) * ld;
+            dx[c] = dexp[16 * cg + c];
         }
-        double x[8];
+        double x[16];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) x[c] = src0[coff[c]];
+        for (int c = 0; c < 16; ++c) x[c] = src0[coff[c]];
         for (int t = 0; t < nblk; ++t) {
             const int buf = t & 1;
             int m = split::kNoExp;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) m = max(m, split::exp_bound(x[c], -dx[c]));
+            for (int c = 0; c < 16; ++c) m = max(m, split::exp_bound(x[c], -dx[c]));
             rmax[(buf * CG + cg) * MB + r] = m;
             bar_sync<nb::kProd, NP>();
             int E = split::kNoExp;
 #pragma unroll
             for (int g = 0; g < CG; ++g) E = max(E, rmax[(buf * CG + g) * MB + r]);
             if (E == split::kNoExp) E = 0;
-            unsigned long long z[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) z[c] = split::fixed_biased(x[c], -dx[c], E);
-            // prefetch the next block's entries while this one is split
-            if (t + 1 < nblk) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) x[c] = src0[coff[c] + (size_t)(t + 1) * MB];
-            }
             if (t >= 2) bar_sync_buf<nb::kEmpty0, NT>(buf);   // consumers are done with block t - 2
             if (cg == 0) rexp[buf * MB + r] = E;
-            uint16_t *dst = As + (size_t)buf * split::kSlices * S::kUSliceA + r * S::kULd + 8 * cg;
-            const unsigned long long z0[4] = {z[0], z[1], z[2], z[3]};
-            const unsigned long long z1[4] = {z[4], z[5], z[6], z[7]};
-            store_digits4(dst, S::kUSliceA, z0);
-            store_digits4(dst + 4, S::kUSliceA, z1);
+            uint16_t *dst = As + (size_t)buf * split::kSlices * S::kUSliceA + r * S::kULd + 16 * cg;
+            // four columns at a time: digits of this block, then the next
+            // block's entries of those columns are requested
+#pragma unroll
+            for (int c = 0; c < 16; c += 4) {
+                const unsigned long long z[4] = {split::fixed_biased(x[c], -dx[c], E),
+                                                 split::fixed_biased(x[c + 1], -dx[c + 1], E),
+                                                 split::fixed_biased(x[c + 2], -dx[c + 2], E),
+                                                 split::fixed_biased(x[c + 3], -dx[c + 3], E)};
+                if (t + 1 < nblk) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) x[c + u] = src0[coff[c + u] + (size_t)(t + 1) * MB];
+                }
+                store_digits4(dst + c, S::kUSliceA, z);
+            }
             bar_arrive_buf<nb::kFull0, NT>(buf);
         }
     } else {
         // ---------------- consumers ----------------
-        const int cw = (threadIdx.x - NP) >> 5;        // 0..3: tile
+        const int cw = (threadIdx.x - NP) >> 5;        // 0..7: tile
         constexpr int TN = BB / 16;
         const int tm = cw / TN, tn = cw % TN;
         int gcol[8];
