@@ -78,16 +78,24 @@ __device__ __forceinline__ unsigned long long fixed_biased(double x, int off, in
     return bits < 0 ? kBias - y : kBias + y;
 }
 
-// bf16 bit pattern of the digit i of Z (value in [-64, 64]), in the low 16 bits.
+// The biased digit u_i of Z: u_0 = Z >> 56 in [0, 128], u_i = bits [56-7i,
+// 63-7i) in [0, 127]; the digit is u_i - 64.
 template <int I>
-__device__ __forceinline__ uint32_t digit_bf16(unsigned long long z) {
-    const uint32_t u = I == 0 ? (uint32_t)(z >> 56) : (uint32_t)((z >> (56 - 7 * I)) & 127ull);
-    const float f = __fsub_rn(__uint_as_float(0x4B000000u | u), 8388672.0f);   // u - 64, exact
-    return __float_as_uint(f) >> 16;                                          // exact bf16
+__device__ __forceinline__ uint32_t digit_field(unsigned long long z) {
+    return I == 0 ? (uint32_t)(z >> 56) : (uint32_t)((z >> (56 - 7 * I)) & 127ull);
 }
 
-// Two digits (columns c, c+1 of the K axis) packed for one 32-bit store.
-__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) { return lo | (hi << 16); }
+// Digit I of z0 (low half) and of z1 (high half) as two exact bf16 values in
+// one 32-bit word: 0x4300 | u is the bf16 pattern of 128 + u for u in
+// [0, 128] (u = 128 carries into the exponent: 0x4380 = 256), and one
+// bf16x2 FMA subtracts 192 from both halves exactly.
+template <int I>
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long z0, unsigned long long z1) {
+    const uint32_t biased = __byte_perm(digit_field<I>(z0), digit_field<I>(z1), 0x5410) | 0x43004300u;
+    uint32_t d;
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(biased), "r"(0x3F803F80u), "r"(0xC340C340u));
+    return d;
+}
 
 // ---------------------------------------------------------------------------
 // Warp-level tile: lev[L][e] += sum over K of the level-L digit products for a

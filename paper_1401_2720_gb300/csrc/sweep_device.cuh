@@ -181,7 +181,7 @@ __device__ __forceinline__ void split_right_factor(const double *W, const double
             const unsigned long long z1 = split::fixed_biased(w[j + 1], ver ? 0 : dx[j + 1], F);
 #define JSVD_SPLIT_STORE(I) \
     *reinterpret_cast<uint32_t *>(o + (I) * BB * LD + j) = \
-        split::pack2(split::digit_bf16<I>(z0), split::digit_bf16<I>(z1));
+        split::digit_pair<I>(z0, z1);
             JSVD_SPLIT_STORE(0) JSVD_SPLIT_STORE(1) JSVD_SPLIT_STORE(2) JSVD_SPLIT_STORE(3) JSVD_SPLIT_STORE(4)
             JSVD_SPLIT_STORE(5) JSVD_SPLIT_STORE(6) JSVD_SPLIT_STORE(7) JSVD_SPLIT_STORE(8)
 #undef JSVD_SPLIT_STORE

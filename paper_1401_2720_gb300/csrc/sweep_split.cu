@@ -59,8 +59,7 @@ constexpr size_t update_split_smem() {
 __device__ __forceinline__ void store_digits4(uint16_t *dst, int slice_stride, const unsigned long long (&z)[4]) {
 #define JSVD_D4(I)                                                                                            \
     *reinterpret_cast<uint2 *>(dst + (I) * slice_stride) =                                                    \
-        make_uint2(split::pack2(split::digit_bf16<I>(z[0]), split::digit_bf16<I>(z[1])),                       \
-                   split::pack2(split::digit_bf16<I>(z[2]), split::digit_bf16<I>(z[3])));
+        make_uint2(split::digit_pair<I>(z[0], z[1]), split::digit_pair<I>(z[2], z[3]));
     JSVD_D4(0) JSVD_D4(1) JSVD_D4(2) JSVD_D4(3) JSVD_D4(4) JSVD_D4(5) JSVD_D4(6) JSVD_D4(7) JSVD_D4(8)
 #undef JSVD_D4
 }
@@ -179,7 +178,7 @@ __global__ void __launch_bounds__(SplitCfg<BB>::kGThreads, 1) gram_split(PStepAr
                 if (t + 1 < nsub) x[c] = *reinterpret_cast<const double2 *>(src[c] + (size_t)(t + 1) * S::kSub);
 #define JSVD_G2(I)                                                                                  \
     *reinterpret_cast<uint32_t *>(dst + (I) * S::kGSlice + c * S::kGLd) =                           \
-        split::pack2(split::digit_bf16<I>(z0), split::digit_bf16<I>(z1));
+        split::digit_pair<I>(z0, z1);
                 JSVD_G2(0) JSVD_G2(1) JSVD_G2(2) JSVD_G2(3) JSVD_G2(4) JSVD_G2(5) JSVD_G2(6) JSVD_G2(7) JSVD_G2(8)
 #undef JSVD_G2
             }
