@@ -264,6 +264,23 @@ def run_batched(args) -> None:
     flops = prof["other"][2] / args.steps
     # accuracy spot check against the planted spectra (normwise per matrix)
     err = max(float(np.max(np.abs(s.cpu().numpy() - st)) / st[0]) for s, st in zip(pk.unpack_n(S), sig))
+    # the plain form on the same matrices, one solve per matrix (single-matrix
+    # entry point, default options), on a fixed sample: outside the timed region
+    sample = list(range(0, len(mats), max(1, len(mats) // args.plain_sample)))[: args.plain_sample]
+    dev_mats = [torch.from_numpy(np.ascontiguousarray(mats[i].T)).to(dev).t() for i in sample]
+    for a in dev_mats[:8]:
+        J.svd(a)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for i, a in zip(sample, dev_mats):
+        _, s_i, _ = J.svd(a)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1) / len(sample)
+    sample_fwd_share = sum(mats[i].shape[0] * mats[i].shape[1] ** 2 for i in sample) / sum(
+        a.shape[0] * a.shape[1] ** 2 for a in mats) * len(mats) / len(sample)
     line = {
         "metric": METRIC, "value": ms_step / 1e3 / len(pk), "unit": "s/matrix", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
@@ -274,6 +291,12 @@ def run_batched(args) -> None:
                          {f"n in {autotune.BUCKETS[k]}": v for k, v in sorted(tuned.items())}),
                    "autotune_s": None if tuned is None else tune_s},
         "matrices_per_s": len(pk) / (ms_step / 1e3),
+        "plain_form": {"matrices": len(sample), "ms_per_matrix": plain_ms,
+                       "forward_matrices_per_s": 1e3 / plain_ms,
+                       "batched_forward_matrices_per_s": len(pk) / (fwd / 1e3),
+                       "note": "the same matrices solved one at a time through jsvd.svd (forward only); an evenly "
+                               "spaced sample of the batch, whose m n^2 work is "
+                               f"{sample_fwd_share:.2f}x the batch average"},
         "forward_ms": fwd, "backward_ms": bwd, "tflops": flops / (ms_step * 1e-3) / 1e12,
         "sweeps_max": max(i["sweeps"] for i in infos), "sweeps_mean": statistics.mean(i["sweeps"] for i in infos),
         "converged": all(i["converged"] for i in infos), "max_normwise_sigma_err_vs_planted": err,
@@ -510,6 +533,8 @@ def main():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="graded8192", choices=sorted(WORKLOADS) + ["batched4096"])
     p.add_argument("--batch", type=int, default=4096)
+    p.add_argument("--plain-sample", type=int, default=256,
+                   help="batched workload: matrices solved one at a time for the plain-form comparison")
     p.add_argument("--b", type=int, default=None,
                    help="block width (default 32; the batched workload autotunes it per bucket of n)")
     p.add_argument("--strategy", default=None, help="pivot strategy (default rR; modulus for small512)")

@@ -470,10 +470,13 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
 
     jsvd_info inf{};
     inf.b = b;
-    // Block sweeps until a sweep has no proper rotation (Sec. 4.5) or the limit.
-    auto sweep_loop = [&](int limit, int *done, int *conv) -> int {
+    // Block sweeps until a sweep has no proper rotation (Sec. 4.5), the limit,
+    // or (stop_frac > 0) a sweep with fewer proper rotations than stop_frac
+    // times the first sweep's.
+    auto sweep_loop = [&](int limit, int *done, int *conv, double stop_frac) -> int {
         *done = 0;
         *conv = 0;
+        unsigned long long first_proper = 0;
         while (*done < limit) {
             cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
             const bool side = side_streams && a.V != nullptr && !a.split;
@@ -560,6 +563,8 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
                         a.fp32 ? "fp32" : "fp64", *done, host_counters[kCntRot], host_counters[kCntProper],
                         host_counters[kCntUpdated], off);
             if (host_counters[kCntProper] == 0) { *conv = 1; break; }
+            if (*done == 1) first_proper = host_counters[kCntProper];
+            if (stop_frac > 0.0 && (double)host_counters[kCntProper] < stop_frac * (double)first_proper) break;
         }
         return 0;
     };
@@ -575,7 +580,10 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         prof_launches[4] += 2;
         a.G = G32; a.V = V32; a.fp32 = 1; a.eps = 0x1p-24; a.split = 0;
         int low_done = 0, low_conv = 0;
-        if ((rc = sweep_loop(o.max_sweeps, &low_done, &low_conv))) return rc;
+        // The FP32 stage is a preconditioner: it ends once a sweep rotates
+        // less than 1 % as much as its first one (its last sweeps only polish
+        // what the FP64 sweeps redo at FP64 accuracy anyway)
+        if ((rc = sweep_loop(o.max_sweeps, &low_done, &low_conv, 0.01))) return rc;
         inf.sweeps_low = low_done;
         // Stage 2: Q = polar factor of V32 in FP64, G := G Q, V := Q.
         if ((rc = polar_and_apply(G, g_rows, n_pad, nplus_w, V32, v_rows, V, v_rows))) return rc;
@@ -589,7 +597,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         prof_launches[4] += 1;
     }
     int converged = 0, sweeps = 0;
-    if ((rc = sweep_loop(o.max_sweeps, &sweeps, &converged))) return rc;
+    if ((rc = sweep_loop(o.max_sweeps, &sweeps, &converged, 0.0))) return rc;
     inf.sweeps = sweeps;
     inf.converged = converged;
 

@@ -213,8 +213,33 @@ __device__ __forceinline__ void nbar_arrive() {
     asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
 }
 
-template <int BB>
-__device__ __forceinline__ void jacobi_sweep_pipelined(double *A, double *B, const unsigned char *tab, int P, int Q,
+// Element arithmetic of the inner sweep in the type RT of R and V': FP64, or
+// FP32 in the first stage of the mixed solver.  The rotation parameters are
+// always computed in FP64 (Eqs. (4.3)-(4.6)) and rounded to RT to be applied.
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add_t(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_t(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double mul_t(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_t(float a, float b) { return __fmul_rn(a, b); }
+
+// Eq. (4.1) / (4.2) on one row in RT: the FMA form of rot_apply with cs, tn
+// given in RT; `proper` is cs != 1 of the FP64 parameters.
+template <typename RT>
+__device__ __forceinline__ void rot_apply_t(RT &x, RT &y, bool hyperbolic, RT cs, RT tn, bool proper) {
+    const RT xn = fma_t(hyperbolic ? tn : -tn, y, x);
+    const RT yn = fma_t(tn, x, y);
+    if (proper) {
+        x = mul_t(cs, xn);
+        y = mul_t(cs, yn);
+    } else {
+        x = xn;
+        y = yn;
+    }
+}
+
+template <int BB, typename RT = double>
+__device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsigned char *tab, int P, int Q,
                                                        int b, int nplus, int bord_lo, int bord_hi, double c_eps,
                                                        int &my_rot, int &my_proper, int &changed) {
     using C = Cfg<BB>;
@@ -222,7 +247,7 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(double *A, double *B, con
     constexpr int NT = 2 * NH;
     constexpr int NP = BB / 2;                // pairs per inner step
     __shared__ double s_cs[2][NP], s_tn[2][NP];
-    __shared__ int s_fl[2][NP];               // bit 0: rotate, bit 1: swap, bit 2: hyperbolic
+    __shared__ int s_fl[2][NP];               // bit 0: rotate, 1: swap, 2: hyperbolic, 3: cs != 1
     const int tid = threadIdx.x;
     if (tid < NH) {
         // ---------------- R side ----------------
@@ -232,22 +257,23 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(double *A, double *B, con
             const int slot = st & 1;
             const int p = tab[2 * (st * (BB / 2) + y)];
             const int q = tab[2 * (st * (BB / 2) + y) + 1];
-            double *rp = B + p * C::kLd, *rq = B + q * C::kLd;
-            double hpp = 0.0, hqq = 0.0, hpq = 0.0;
+            RT *rp = B + p * C::kLd, *rq = B + q * C::kLd;
+            RT tpp = 0, tqq = 0, tpq = 0;
 #pragma unroll
             for (int k = 0; k < C::kRowsPerLane; ++k) {
                 const int r = g + k * C::kLanesPerPair;
-                const double x = rp[r], z = rq[r];
-                hpp = __fma_rn(x, x, hpp);
-                hqq = __fma_rn(z, z, hqq);
-                hpq = __fma_rn(x, z, hpq);
+                const RT x = rp[r], z = rq[r];
+                tpp = fma_t(x, x, tpp);
+                tqq = fma_t(z, z, tqq);
+                tpq = fma_t(x, z, tpq);
             }
 #pragma unroll
             for (int off = C::kLanesPerPair / 2; off > 0; off >>= 1) {
-                hpp = __dadd_rn(hpp, __shfl_xor_sync(0xffffffffu, hpp, off));
-                hqq = __dadd_rn(hqq, __shfl_xor_sync(0xffffffffu, hqq, off));
-                hpq = __dadd_rn(hpq, __shfl_xor_sync(0xffffffffu, hpq, off));
+                tpp = add_t(tpp, __shfl_xor_sync(0xffffffffu, tpp, off));
+                tqq = add_t(tqq, __shfl_xor_sync(0xffffffffu, tqq, off));
+                tpq = add_t(tpq, __shfl_xor_sync(0xffffffffu, tpq, off));
             }
+            const double hpp = (double)tpp, hqq = (double)tqq, hpq = (double)tpq;
             const int gp = block_col(P, Q, b, p), gq = block_col(P, Q, b, q);
             const bool hyp = gp < nplus && gq >= nplus;
             const bool border = (gp >= bord_lo && gp < bord_hi) || (gq >= bord_lo && gq < bord_hi);
@@ -260,21 +286,23 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(double *A, double *B, con
                 const double nqq = rho ? __fma_rn(rot.tn, hpq, hqq) : hqq;
                 swap = (gq < nplus && npp < nqq) || (gp >= nplus && npp > nqq);
             }
+            const RT cs_t = (RT)rot.cs, tn_t = (RT)rot.tn;
+            const bool proper = is_proper(rot);
             if (st >= 2) {
                 if (slot) nbar_sync<jb::kEmpty0 + 1, NT>(); else nbar_sync<jb::kEmpty0, NT>();
             }
             if (g == 0) {
                 s_cs[slot][y] = rot.cs;
                 s_tn[slot][y] = rot.tn;
-                s_fl[slot][y] = (rho ? 1 : 0) | (swap ? 2 : 0) | (hyp ? 4 : 0);
+                s_fl[slot][y] = (rho ? 1 : 0) | (swap ? 2 : 0) | (hyp ? 4 : 0) | (proper ? 8 : 0);
             }
             if (slot) nbar_arrive<jb::kFull0 + 1, NT>(); else nbar_arrive<jb::kFull0, NT>();
             if (rho || swap) {
 #pragma unroll
                 for (int k = 0; k < C::kRowsPerLane; ++k) {
                     const int r = g + k * C::kLanesPerPair;
-                    double x = rp[r], z = rq[r];
-                    if (rho) rot_apply(x, z, hyp, rot);
+                    RT x = rp[r], z = rq[r];
+                    if (rho) rot_apply_t(x, z, hyp, cs_t, tn_t, proper);
                     if (swap) {
                         rp[r] = z; rq[r] = x;
                     } else {
@@ -285,7 +313,7 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(double *A, double *B, con
             }
             if (g == 0 && rho) {
                 ++my_rot;
-                if (is_proper(rot)) ++my_proper;
+                if (proper) ++my_proper;
             }
             nbar_sync<jb::kRSide, NH>();
         }
@@ -299,19 +327,20 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(double *A, double *B, con
             const int p = tab[2 * (st * (BB / 2) + y)];
             const int q = tab[2 * (st * (BB / 2) + y) + 1];
             if (slot) nbar_sync<jb::kFull0 + 1, NT>(); else nbar_sync<jb::kFull0, NT>();
-            const Rot rot{s_cs[slot][y], s_tn[slot][y]};
+            const double cs = s_cs[slot][y], tn = s_tn[slot][y];
             const int fl = s_fl[slot][y];
             if (st + 2 < BB - 1) {
                 if (slot) nbar_arrive<jb::kEmpty0 + 1, NT>(); else nbar_arrive<jb::kEmpty0, NT>();
             }
-            const bool rho = fl & 1, swap = fl & 2, hyp = fl & 4;
-            double *wp = A + p * C::kLd, *wq = A + q * C::kLd;
+            const bool rho = fl & 1, swap = fl & 2, hyp = fl & 4, proper = fl & 8;
+            const RT cs_t = (RT)cs, tn_t = (RT)tn;
+            RT *wp = A + p * C::kLd, *wq = A + q * C::kLd;
             if (rho || swap) {
 #pragma unroll
                 for (int k = 0; k < C::kRowsPerLane; ++k) {
                     const int r = g + k * C::kLanesPerPair;
-                    double u = wp[r], w = wq[r];
-                    if (rho) rot_apply(u, w, hyp, rot);
+                    RT u = wp[r], w = wq[r];
+                    if (rho) rot_apply_t(u, w, hyp, cs_t, tn_t, proper);
                     if (swap) {
                         wp[r] = w; wq[r] = u;
                     } else {
@@ -342,7 +371,7 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(double *A, double *B, con
 // of the pair's columns of G are reset (the split update recomputes them).  Global columns in [bord_lo, bord_hi) are the
 // identity border: they are exactly orthogonal to everything, and they are
 // neither rotated nor swapped, so they keep their positions.
-template <int BB, int NT = Cfg<BB>::kJacThreads>
+template <int BB, int NT = Cfg<BB>::kJacThreads, typename RT = double>
 __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int chunks,
                                             const unsigned char *__restrict__ inner, int P, int Q, int b,
                                             int nplus, int bord_lo, int bord_hi, int inner_sweeps, double eps,
@@ -432,15 +461,17 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
         __syncthreads();
     }
 
-    // (4) R = L^T into B; V' = I into A
+    // (4) R = L^T into B; V' = I into A (both in RT from here on)
+    RT *Rt = reinterpret_cast<RT *>(B);
+    RT *Vt = reinterpret_cast<RT *>(A);
     for (int e = tid; e < BB * BB; e += NT) {
         const int i = e % BB, j = e / BB;
-        B[i + j * C::kLd] = (i <= j) ? A[j + i * C::kLd] : 0.0;
+        Rt[i + j * C::kLd] = (i <= j) ? (RT)A[j + i * C::kLd] : (RT)0;
     }
     __syncthreads();
     for (int e = tid; e < BB * BB; e += NT) {
         const int i = e % BB, j = e / BB;
-        A[i + j * C::kLd] = (i == j) ? 1.0 : 0.0;
+        Vt[i + j * C::kLd] = (i == j) ? (RT)1 : (RT)0;
     }
     __syncthreads();
 
@@ -450,10 +481,11 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     if constexpr (NT == 2 * C::kJacThreads) {
         // one inner sweep, V' rotated one step behind R by the second half of
         // the threads
-        jacobi_sweep_pipelined<BB>(A, B, tab, P, Q, b, nplus, bord_lo, bord_hi, c_eps, my_rot, my_proper, changed);
+        jacobi_sweep_pipelined<BB, RT>(Vt, Rt, tab, P, Q, b, nplus, bord_lo, bord_hi, c_eps, my_rot, my_proper,
+                                       changed);
         sweeps_done = 1;
     } else {
-    static_assert(NT == C::kJacThreads, "thread count");
+    static_assert(NT == C::kJacThreads && sizeof(RT) == sizeof(double), "thread count, FP64 inner sweep");
     const int y = tid / C::kLanesPerPair;
     const int g = tid % C::kLanesPerPair;
     for (int sw = 0; sw < inner_sweeps; ++sw) {
@@ -521,9 +553,10 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     const int any_change = __syncthreads_or(changed);
     for (int e = tid; e < BB * BB; e += NT) {
         const int i = e % BB, j = e / BB;
-        vp[e] = A[i + j * C::kLd];
+        vp[e] = (double)Vt[i + j * C::kLd];
     }
-    if (bsl && any_change) split_right_factor<BB, NT>(A, hdiag, dx, bsl, bexp, dexp);
+    if constexpr (sizeof(RT) == sizeof(double))
+        if (bsl && any_change) split_right_factor<BB, NT>(A, hdiag, dx, bsl, bexp, dexp);
     // the update of G rewrites these columns and max-reduces their new bounds
     if (gexp && any_change)
         for (int k = tid; k < BB; k += NT) gexp[block_col(P, Q, b, k)] = split::kNoExp;

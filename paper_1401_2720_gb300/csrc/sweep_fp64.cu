@@ -19,14 +19,16 @@ __global__ void __launch_bounds__(Cfg<BB>::kGramThreads) gram_partial(PStepArgs 
 }
 
 // NT = kJacThreads: any number of inner sweeps; NT = 2 kJacThreads: one inner
-// sweep with V' rotated by a second thread group (jacobi_sweep_pipelined).
-template <int BB, int NT>
+// sweep with V' rotated by a second thread group (jacobi_sweep_pipelined),
+// R and V' held in RT (float in the FP32 sweeps of the mixed solver; the
+// rotation parameters, Cholesky and counters stay FP64).
+template <int BB, int NT, typename RT = double>
 __global__ void __launch_bounds__(NT) pair_jacobi(PStepArgs a) {
     extern __shared__ __align__(16) double smem[];
     const int pair = blockIdx.x;
     const int P = a.table[2 * (a.step * a.npairs + pair)];
     const int Q = a.table[2 * (a.step * a.npairs + pair) + 1];
-    jacobi_unit<BB, NT>(a.part + (size_t)pair * a.g_chunks * Cfg<BB>::kPacked, a.g_chunks, a.inner, P, Q, a.b,
+    jacobi_unit<BB, NT, RT>(a.part + (size_t)pair * a.g_chunks * Cfg<BB>::kPacked, a.g_chunks, a.inner, P, Q, a.b,
                     a.nplus, a.bord_lo, a.bord_hi, a.inner_sweeps, a.eps, a.vprime + (size_t)pair * BB * BB, a.vflag + pair,
                     a.counters, smem, a.split ? a.bslice + (size_t)pair * 2 * split_b_elems<BB>() : nullptr,
                     a.split ? a.bexp + (size_t)pair * 2 * BB : nullptr, a.split ? a.dexp + (size_t)pair * BB : nullptr,
@@ -64,6 +66,8 @@ static void configure_once() {
                          (int)jacobi_smem_bytes<BB>());
     cudaFuncSetAttribute(pair_jacobi<BB, 2 * Cfg<BB>::kJacThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)jacobi_smem_bytes<BB>());
+    cudaFuncSetAttribute(pair_jacobi<BB, 2 * Cfg<BB>::kJacThreads, float>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem_bytes<BB>());
     cudaFuncSetAttribute(block_update<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)update_smem_bytes<BB, T>());
     done[dev] = true;
@@ -81,7 +85,9 @@ static void launch_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
         }
         case Phase::Jacobi: {
             const size_t sm = jacobi_smem_bytes<BB>();
-            if (a.inner_sweeps == 1)
+            if (a.inner_sweeps == 1 && a.fp32)
+                pair_jacobi<BB, 2 * C::kJacThreads, float><<<a.npairs, 2 * C::kJacThreads, sm, s>>>(a);
+            else if (a.inner_sweeps == 1)
                 pair_jacobi<BB, 2 * C::kJacThreads><<<a.npairs, 2 * C::kJacThreads, sm, s>>>(a);
             else
                 pair_jacobi<BB, C::kJacThreads><<<a.npairs, C::kJacThreads, sm, s>>>(a);
