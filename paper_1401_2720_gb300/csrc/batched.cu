@@ -24,20 +24,23 @@
 #include "driver.h"
 #include "jsvd.h"
 #include "jsvd_internal.h"
+#include "split_kernels.cuh"
 #include "sweep_device.cuh"
 
 using namespace jsvd;
 
 namespace {
 
-constexpr int kRowPad = 8;        // rows of G and V are padded to multiples of 8
+constexpr int kRowPad = 32;       // rows of G and V are padded to multiples of 32 (zero rows)
 constexpr int kRing = 4;          // V' slots: the V update of step s may lag the main branch by 3 steps
 constexpr int kMaxSortCols = 1024;
 
 struct BMat {
     int m, n, nb, b, n_pad, k, m_b, g_rows, v_rows, g_chunks, npairs, ug, uv;
+    int gc_s, ug_s, uv_s;      // split contractions: Gram partials (256 rows), update units (512 rows)
     int tab_off, vflag_off;
     long long g_off, v_off, part_off, vp_off, col_off;
+    long long bsl_off, bex_off, dex_off;   // split right factors of the matrix's pairs (per ring slot)
     long long a_off, s_off, u_off, vo_off;
 };
 
@@ -78,6 +81,10 @@ struct BArgs {
     unsigned long long *counters; // kCntSize per matrix
     BStat *stats;
     int inner_sweeps;
+    int split;                    // tensor-core contractions (split_kernels.cuh)
+    uint16_t *bsl;                // split right factors of this ring slot
+    int *bexp, *dexp;
+    int *gexp;                    // column exponent bounds, indexed by col_off + column
 };
 
 template <int BB>
@@ -106,9 +113,14 @@ __global__ void __launch_bounds__(NT) kb_jacobi(BArgs a, int off, int count, int
     const int pair = blockIdx.x - u.start;
     const int P = a.tables[M.tab_off + 2 * (step * M.npairs + pair)];
     const int Q = a.tables[M.tab_off + 2 * (step * M.npairs + pair) + 1];
-    jacobi_unit<BB, NT>(a.part + M.part_off + (size_t)pair * M.g_chunks * Cfg<BB>::kPacked, M.g_chunks, a.inner, P,
+    const int chunks = a.split ? M.gc_s : M.g_chunks;
+    jacobi_unit<BB, NT>(a.part + M.part_off + (size_t)pair * chunks * Cfg<BB>::kPacked, chunks, a.inner, P,
                     Q, M.b, M.n_pad, M.n, M.n_pad, a.inner_sweeps, kEps, a.vprime + M.vp_off + (size_t)pair * BB * BB,
-                    a.vflag + M.vflag_off + pair, a.counters + (size_t)u.mat * kCntSize, smem);
+                    a.vflag + M.vflag_off + pair, a.counters + (size_t)u.mat * kCntSize, smem,
+                    a.split ? a.bsl + M.bsl_off + (size_t)pair * 2 * split_b_elems<BB>() : nullptr,
+                    a.split ? a.bexp + M.bex_off + (size_t)pair * 2 * BB : nullptr,
+                    a.split ? a.dexp + M.dex_off + (size_t)pair * BB : nullptr,
+                    a.split ? a.gexp + M.col_off : nullptr);
 }
 
 // which = 0: rows of G, which = 1: rows of V
@@ -133,6 +145,70 @@ __global__ void __launch_bounds__(kUpdThreads) kb_update(BArgs a, int off, int c
         X = a.V + M.v_off; ld = M.v_rows; r0 = c * RU; valid = min(RU, M.v_rows - r0);
     }
     update_unit<BB, double>(X, ld, r0, valid, P, Q, M.b, a.vprime + M.vp_off + (size_t)pair * BB * BB, smem);
+}
+
+// Split-contraction Gram: unit = (matrix, pair, 256-row partial).
+template <int BB>
+__global__ void __launch_bounds__(SplitCfg<BB>::kGThreads, 1) kb_gram_split(BArgs a, int off, int count, int step) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BUnit u = a.units[off + find_unit(a.units + off, count, blockIdx.x)];
+    const BMat M = a.mats[u.mat];
+    if (!a.stats[u.mat].active) return;
+    const int local = blockIdx.x - u.start;
+    const int pair = local / M.gc_s, chunk = local % M.gc_s;
+    const int P = a.tables[M.tab_off + 2 * (step * M.npairs + pair)];
+    const int Q = a.tables[M.tab_off + 2 * (step * M.npairs + pair) + 1];
+    const int r0 = chunk * kGramRowsSplit;
+    gram_split_body<BB>(a.G + M.g_off, M.g_rows, P, Q, M.b, a.gexp + M.col_off, (size_t)r0,
+                        min(kGramRowsSplit, M.g_rows - r0),
+                        a.part + M.part_off + (size_t)pair * M.gc_s * Cfg<BB>::kPacked, chunk, smem_raw);
+}
+
+// Split-contraction update, which = 0: rows of G, which = 1: rows of V;
+// unit = (matrix, pair, kUpdRowsPerCta rows).
+template <int BB>
+__global__ void __launch_bounds__(32 * SplitCfg<BB>::kUpdWarps) kb_update_split(BArgs a, int off, int count, int step,
+                                                                              int which) {
+    using S = SplitCfg<BB>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BUnit u = a.units[off + find_unit(a.units + off, count, blockIdx.x)];
+    const BMat M = a.mats[u.mat];
+    if (!a.stats[u.mat].active) return;
+    const int local = blockIdx.x - u.start;
+    const int per = which ? M.uv_s : M.ug_s;
+    const int pair = local / per, c = local % per;
+    if (!a.vflag[M.vflag_off + pair]) return;
+    const int P = a.tables[M.tab_off + 2 * (step * M.npairs + pair)];
+    const int Q = a.tables[M.tab_off + 2 * (step * M.npairs + pair) + 1];
+    double *X = which ? a.V + M.v_off : a.G + M.g_off;
+    const int ld = which ? M.v_rows : M.g_rows;
+    const int r0 = c * S::kUpdRowsPerCta;
+    update_split_body<BB, true>(X, ld, (size_t)r0, min(S::kUpdRowsPerCta, ld - r0), P, Q, M.b,
+                          a.bsl + M.bsl_off + ((size_t)pair * 2 + which) * split_b_elems<BB>(),
+                          a.bexp + M.bex_off + ((size_t)pair * 2 + which) * BB,
+                          which ? nullptr : a.dexp + M.dex_off + (size_t)pair * BB,
+                          which ? nullptr : a.gexp + M.col_off, smem_raw);
+}
+
+// Exponent bounds of every column of every matrix's G (one warp per column).
+__global__ void kb_col_maxexp(const BMat *mats, int batch, const long long *col_start, long long total_cols,
+                              const double *G, int *gexp) {
+    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (w >= total_cols) return;
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (col_start[mid] <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    const BMat M = mats[lo];
+    const int c = (int)(w - col_start[lo]);
+    const double *g = G + M.g_off + (size_t)c * M.g_rows;
+    int e = split::kNoExp;
+    for (int r = lane; r < M.g_rows; r += 32) e = max(e, split::exp_bound(g[r], 0));
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0) gexp[w] = e;
 }
 
 // Bordered copy of every A_i into its G_i, V_i = I, all matrices active.
@@ -334,11 +410,13 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         return JSVD_ERR_UNSUPPORTED;
     }
     int rc;
+    const bool split = o.contraction == JSVD_CONTRACT_SPLIT;
     // ---- per-matrix layout ---------------------------------------------------
     std::vector<BMat> mats(batch);
     std::vector<int> tables;
     std::vector<std::pair<int, int>> tab_keys;  // (nb, offset)
     long long g_tot = 0, v_tot = 0, p_tot = 0, vp_tot = 0, col_tot = 0, out_tot = 0;
+    long long bsl_tot = 0, bex_tot = 0, dex_tot = 0;
     int vf_tot = 0;
     std::vector<long long> col_start(batch), out_start(batch);
     for (int i = 0; i < batch; ++i) {
@@ -366,6 +444,13 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         const int BB = 2 * M.b, RU = 4096 / BB;
         M.ug = (M.g_rows + RU - 1) / RU;
         M.uv = (M.v_rows + RU - 1) / RU;
+        M.gc_s = (M.g_rows + kGramRowsSplit - 1) / kGramRowsSplit;
+        M.ug_s = (M.g_rows + SplitCfg<64>::kUpdRowsPerCta - 1) / SplitCfg<64>::kUpdRowsPerCta;
+        M.uv_s = (M.v_rows + SplitCfg<64>::kUpdRowsPerCta - 1) / SplitCfg<64>::kUpdRowsPerCta;
+        const long long belems = BB == 16 ? split_b_elems<16>() : BB == 32 ? split_b_elems<32>() : split_b_elems<64>();
+        M.bsl_off = bsl_tot; bsl_tot += (long long)M.npairs * 2 * belems;
+        M.bex_off = bex_tot; bex_tot += (long long)M.npairs * 2 * BB;
+        M.dex_off = dex_tot; dex_tot += (long long)M.npairs * BB;
         int toff = -1;
         for (auto &kv : tab_keys)
             if (kv.first == M.nb) toff = kv.second;
@@ -407,8 +492,10 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
                 for (int i = 0; i < batch; ++i) {
                     const BMat &M = mats[i];
                     if (2 * M.b != BB || s >= M.nb - 1) continue;
-                    const int cnt = kind == 0 ? M.npairs * M.g_chunks
-                                  : kind == 1 ? M.npairs : kind == 2 ? M.npairs * M.ug : M.npairs * M.uv;
+                    const int cnt = kind == 0 ? M.npairs * (split ? M.gc_s : M.g_chunks)
+                                  : kind == 1 ? M.npairs
+                                  : kind == 2 ? M.npairs * (split ? M.ug_s : M.ug)
+                                              : M.npairs * (split ? M.uv_s : M.uv);
                     units.push_back(BUnit{i, l.units});
                     l.units += cnt;
                     ++l.count;
@@ -424,9 +511,11 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         sizeof(double) * std::max<long long>(vp_tot, 1) * kRing, sizeof(int) * std::max(vf_tot, 1) * kRing,
         sizeof(int) * tables.size(), sizeof(unsigned long long) * kCntSize * batch, sizeof(BStat) * batch,
         sizeof(long long) * batch * 2, sizeof(double) * col_tot, sizeof(int) * col_tot, sizeof(int) * col_tot,
-        sizeof(int) * 4};
+        sizeof(int) * 4,
+        split ? sizeof(uint16_t) * bsl_tot * kRing : 16, split ? sizeof(int) * bex_tot * kRing : 16,
+        split ? sizeof(int) * dex_tot * kRing : 16, split ? sizeof(int) * col_tot : 16};
     Buffer *bufs[] = {&b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag, &b_tab, &b_cnt, &b_stat,
-                      &b_starts, &b_sigma, &b_border, &b_perm, &b_misc};
+                      &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &b_bsl, &b_bex, &b_dex, &b_gexp};
     for (size_t j = 0; j < sizeof(bufs) / sizeof(bufs[0]); ++j)
         if ((rc = ensure(*bufs[j], need[j]))) return rc;
     const unsigned char *dinner[3] = {nullptr, nullptr, nullptr};
@@ -461,6 +550,11 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
     ba.counters = (unsigned long long *)b_cnt.ptr;
     ba.stats = (BStat *)b_stat.ptr;
     ba.inner_sweeps = o.inner_sweeps;
+    ba.split = split ? 1 : 0;
+    ba.bsl = (uint16_t *)b_bsl.ptr;
+    ba.bexp = (int *)b_bex.ptr;
+    ba.dexp = (int *)b_dex.ptr;
+    ba.gexp = (int *)b_gexp.ptr;
 
     cudaFuncSetAttribute(kb_gram<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem_bytes<16, double>());
     cudaFuncSetAttribute(kb_gram<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem_bytes<32, double>());
@@ -474,6 +568,15 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
     JSVD_JAC_ATTR(32)
     JSVD_JAC_ATTR(64)
 #undef JSVD_JAC_ATTR
+#define JSVD_SPLIT_ATTR(BBV)                                                                            \
+    cudaFuncSetAttribute(kb_gram_split<BBV>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                         (int)gram_split_smem<BBV>());                                                   \
+    cudaFuncSetAttribute(kb_update_split<BBV>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                         (int)update_split_smem<BBV>());
+    JSVD_SPLIT_ATTR(16)
+    JSVD_SPLIT_ATTR(32)
+    JSVD_SPLIT_ATTR(64)
+#undef JSVD_SPLIT_ATTR
     cudaFuncSetAttribute(kb_update<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem_bytes<16, double>());
     cudaFuncSetAttribute(kb_update<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem_bytes<32, double>());
     cudaFuncSetAttribute(kb_update<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem_bytes<64, double>());
@@ -504,6 +607,9 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { fail("capture"); break; }
         kb_init<<<dim3(64, batch), 256, 0, cs>>>(dm, batch, A, ba.G, ba.V, ba.stats, ba.counters,
                                                  (unsigned long long *)(dmisc + 2));
+        if (split)
+            kb_col_maxexp<<<(unsigned)((col_tot * 32 + 255) / 256), 256, 0, cs>>>(dm, batch, dstarts, col_tot, ba.G,
+                                                                                 ba.gexp);
         if (cudaStreamEndCapture(cs, &g_init) != cudaSuccess) { fail("capture init"); break; }
         cudaGraphNode_t n_init, n_while, n_fin;
         if (cudaGraphAddChildGraphNode(&n_init, graph, nullptr, 0, g_init) != cudaSuccess) { fail("child init"); break; }
@@ -535,17 +641,26 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
             a.inner = dinner[c];
             a.vprime = ba.vprime + (size_t)slot * vp_tot;
             a.vflag = ba.vflag + (size_t)slot * vf_tot;
+            a.bsl = ba.bsl + (size_t)slot * bsl_tot;
+            a.bexp = ba.bexp + (size_t)slot * bex_tot;
+            a.dexp = ba.dexp + (size_t)slot * dex_tot;
             const int off = p.l.offset, cnt = p.l.count, units_n = p.l.units;
             if (units_n <= 0) continue;
             cudaEvent_t *jac_done = &gev[1 + (c * kRing + slot) * 2];
             cudaEvent_t *v_done = jac_done + 1;
             if (p.kind == 0 && p.step >= kRing && Vo) cudaStreamWaitEvent(ms[c], *v_done, 0);
-            if (p.kind == 3) cudaStreamWaitEvent(vs[c], *jac_done, 0);
-            cudaStream_t st = p.kind == 3 ? vs[c] : ms[c];
-            const int prio = p.kind == 3 ? prio_least : prio_greatest;
+            // split contractions update V on the main branch (their update CTAs
+            // slow the latency-bound Jacobi kernel when they run beside it)
+            const bool vside = p.kind == 3 && !split;
+            if (vside) cudaStreamWaitEvent(vs[c], *jac_done, 0);
+            cudaStream_t st = vside ? vs[c] : ms[c];
+            const int prio = vside ? prio_least : prio_greatest;
 #define JSVD_LAUNCH_B(BBV)                                                                              \
     if (p.BB == BBV) {                                                                                  \
-        if (p.kind == 0)                                                                                \
+        if (p.kind == 0 && split)                                                                       \
+            launch_prio(kb_gram_split<BBV>, units_n, SplitCfg<BBV>::kGThreads, gram_split_smem<BBV>(), st, \
+                        prio, a, off, cnt, p.step);                                                     \
+        else if (p.kind == 0)                                                                           \
             launch_prio(kb_gram<BBV>, units_n, Cfg<BBV>::kGramThreads, gram_smem_bytes<BBV, double>(), st, \
                         prio, a, off, cnt, p.step);                                                     \
         else if (p.kind == 1 && ba.inner_sweeps == 1)                                                   \
@@ -554,6 +669,9 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         else if (p.kind == 1)                                                                           \
             launch_prio(kb_jacobi<BBV, Cfg<BBV>::kJacThreads>, units_n, Cfg<BBV>::kJacThreads,          \
                         jacobi_smem_bytes<BBV>(), st, prio, a, off, cnt, p.step);                       \
+        else if (split)                                                                                 \
+            launch_prio(kb_update_split<BBV>, units_n, 32 * SplitCfg<BBV>::kUpdWarps,                   \
+                        update_split_smem<BBV>(), st, prio, a, off, cnt, p.step, p.kind - 2);           \
         else                                                                                            \
             launch_prio(kb_update<BBV>, units_n, kUpdThreads, update_smem_bytes<BBV, double>(), st,     \
                         prio, a, off, cnt, p.step, p.kind - 2);                                         \
@@ -563,7 +681,7 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
             JSVD_LAUNCH_B(64)
 #undef JSVD_LAUNCH_B
             if (p.kind == 1) cudaEventRecord(*jac_done, ms[c]);
-            if (p.kind == 3) cudaEventRecord(*v_done, vs[c]);
+            if (p.kind == 3) cudaEventRecord(*v_done, vside ? vs[c] : ms[c]);
         }
         for (int c = 0; c < 3; ++c) {
             cudaEventRecord(gev[1 + 2 * 3 * kRing + 2 * c], ms[c]);

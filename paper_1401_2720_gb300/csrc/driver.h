@@ -25,7 +25,7 @@ struct jsvd_ctx {
     Buffer bslice, bexp, dexp, gexp;       // split right factors, column exponent bounds (tensor-core contractions)
     Buffer g32, v32, tmp_a, tmp_b, tmp_g;  // mixed precision
     Buffer b_mats, b_units, b_g, b_v, b_part, b_vp, b_vflag, b_tab, b_cnt, b_stat, b_starts, b_sigma,
-        b_border, b_perm, b_misc;          // batched solver
+        b_border, b_perm, b_misc, b_bsl, b_bex, b_dex, b_gexp;   // batched solver
     Buffer adj_w, adj_meta, adj_desc;      // adjoint
     unsigned long long *host_counters = nullptr;  // pinned
     std::map<std::pair<int, int>, Buffer> tables;  // (strategy, order) -> device table

@@ -59,7 +59,8 @@ struct NoallocCtx : jsvd_ctx {
         for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp, &gexp,
                           &g32, &v32, &tmp_a,
                           &tmp_b, &tmp_g, &b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag, &b_tab, &b_cnt,
-                          &b_stat, &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &adj_w, &adj_meta,
+                          &b_stat, &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &b_bsl, &b_bex, &b_dex,
+                          &b_gexp, &adj_w, &adj_meta,
                           &adj_desc}) {
             b->ptr = nullptr;
             b->bytes = 0;

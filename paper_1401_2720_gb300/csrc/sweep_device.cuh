@@ -29,6 +29,7 @@ enum {
 };
 
 constexpr int kGramRows = 128;     // rows of [G_P G_Q] per Gram unit
+constexpr int kGramRowsSplit = 256;   // rows per Gram partial of the split form
 constexpr int kUpdThreads = 256;   // 4x4 output tiles per thread
 
 template <int BB> struct Cfg {

@@ -57,7 +57,6 @@ struct PStepArgs {
     int *gexp;              // [n_pad] exponent bound of every column of G: |g_ij| < 2^gexp[j]
 };
 
-constexpr int kGramRowsSplit = 256;   // rows per Gram partial of the split form (g_rows is a multiple)
 
 constexpr int kRowAlign = 256;     // g_rows, v_rows are multiples of this
 

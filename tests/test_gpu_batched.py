@@ -42,15 +42,18 @@ def test_batched_against_oracle(cuda, b):
         assert np.linalg.norm(a - (u * s) @ v.T) <= 50 * max(n, 2) * EPS * np.linalg.norm(a)
 
 
-def test_batched_equals_single_path(cuda):
-    """Same block width and ordering: the batched solver performs the single
-    path's arithmetic with the FP64 FMA contractions (extra zero rows only add
-    exact zeros), bit for bit."""
-    mats, _, _, _ = _batch(12, seed=2)
+@pytest.mark.parametrize("contraction", ["fp64", "split"])
+@pytest.mark.parametrize("b", [8, 16, 32])
+def test_batched_equals_single_path(cuda, contraction, b):
+    """Same block width, ordering and contraction form: the batched solver
+    performs the single path's arithmetic (extra zero rows only add exact
+    zeros; the split Gram's 256-row partials start at the same rows), bit for
+    bit.  Row counts that end inside a split update block are included."""
+    mats, _, _, _ = _batch(12, seed=2 + b)
     pk = J.Packing([a.shape[0] for a in mats], [a.shape[1] for a in mats])
-    U, S, V = J.svd_batched_packed(pk, pk.pack(mats, cuda), b=8)
+    U, S, V = J.svd_batched_packed(pk, pk.pack(mats, cuda), b=b, contraction=contraction)
     for a, u, s, v in zip(mats, pk.unpack_mn(U), pk.unpack_n(S), pk.unpack_nn(V)):
-        u1, s1, v1 = J.svd(_t(a, cuda), b=8, contraction="fp64")
+        u1, s1, v1 = J.svd(_t(a, cuda), b=b, contraction=contraction)
         assert torch.equal(s, s1) and torch.equal(u, u1) and torch.equal(v, v1)
 
 
