@@ -5,7 +5,9 @@
 //   gram_unit    the lower triangle of [G_P G_Q]^T [G_P G_Q] over one chunk
 //                of rows (Eq. (2.7), split over rows)
 //   jacobi_unit  sum of the chunk partials, Cholesky (Sec. 4.1), M_s inner
-//                sweeps (Sec. 4.3) accumulated into V', counters
+//                sweeps (Sec. 4.3) accumulated into V' (one sweep: R side and
+//                V' side on separate thread groups), counters, and for the
+//                tensor-core contractions the split right factors
 //   update_unit  one chunk of rows of [A_P A_Q] := [A_P A_Q] V' (Eq. (2.9))
 #pragma once
 #include <cuda_runtime.h>

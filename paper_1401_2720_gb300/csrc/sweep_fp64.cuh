@@ -12,13 +12,17 @@
 //   block_update<BB>   [A_P A_Q] := [A_P A_Q] V' for A = G and A = V,
 //                      one row chunk per CTA (Eq. (2.9) / Alg. 4.2).
 //
-// BB = 2b is the order of the pivot block.  In the FP64 form all arithmetic
-// is FP64; the FP64 pipe is the bound on this GPU, so every FMA that is
-// issued does useful work: the Gram kernel computes only the lower triangle,
-// the update skips pairs whose V' is the identity.  In the FP32 form (the
-// first stage of the mixed-precision solver) G and V are float, the Gram's
-// per-chunk sums and the update run in FP32, and the Cholesky factor, the
-// rotations (Eqs. (4.3)-(4.6)) and the counters stay FP64.
+// BB = 2b is the order of the pivot block.  With PStepArgs::split (the
+// default for the FP64 sweeps) the Gram and update launches are the
+// tensor-core kernels gram_split / update_split (sweep_split.cu,
+// split_kernels.cuh), and pair_jacobi also writes the split right factors.
+// In the FP64 FMA form all arithmetic is FP64 and the FP64 pipe is the bound,
+// so every FMA that is issued does useful work: the Gram kernel computes only
+// the lower triangle, the update skips pairs whose V' is the identity.  In the
+// FP32 form (the first stage of the mixed-precision solver) G and V are float,
+// the Gram's per-chunk sums, the update and the inner sweep's dots and
+// rotations run in FP32, and the chunk sums, Cholesky factor, rotation
+// parameters (Eqs. (4.3)-(4.6)) and counters stay FP64.
 #pragma once
 #include <cstdint>
 
