@@ -25,7 +25,7 @@ template <int BB> struct SplitCfg {
     static constexpr int kGThreads = 32 * (kGCons + 2);
     static constexpr int kSub = 32;
     static constexpr int kSubsPerChunk = kGramRowsSplit / kSub;        // 8
-    static constexpr int kChunksPerCta = 2;
+    static constexpr int kChunksPerCta = 4;
     static constexpr int kGLd = kSub + split::kPad;                    // 40
     static constexpr int kGSlice = BB * kGLd;
     static constexpr int kCPT = BB / 4;                                // columns per producer thread
