@@ -439,18 +439,21 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
 
     // (3) Cholesky H = L L^T without pivoting (Sec. 4.1), right-looking:
     // entry (i, j) receives -L(i,k) L(j,k) for k = 0, 1, ... in order, then the
-    // division by the pivot.  A non-positive pivot zeroes its column.
-    for (int k = 0; k < BB; ++k) {
-        if (tid == 0) {
-            const double d = A[k + k * C::kLd];
-            if (d > 0.0) {
-                s_piv = __dsqrt_rn(d);
-            } else {
-                s_piv = 0.0;
-                s_brk += 1;
-            }
+    // division by the pivot.  A non-positive pivot zeroes its column.  The
+    // pivot of column k + 1 is taken by thread 0, which performs that entry's
+    // last update itself (e = 0 of the trailing update), right after it.
+    auto pivot = [&](int k) {
+        const double d = A[k + k * C::kLd];
+        if (d > 0.0) {
+            s_piv = __dsqrt_rn(d);
+        } else {
+            s_piv = 0.0;
+            s_brk += 1;
         }
-        __syncthreads();
+    };
+    if (tid == 0) pivot(0);
+    __syncthreads();
+    for (int k = 0; k < BB; ++k) {
         const double piv = s_piv;
         for (int i = k + tid; i < BB; i += NT)
             A[i + k * C::kLd] = (piv > 0.0) ? (i == k ? piv : __ddiv_rn(A[i + k * C::kLd], piv)) : 0.0;
@@ -461,6 +464,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
             if (i >= j)
                 A[i + j * C::kLd] = __fma_rn(-A[i + k * C::kLd], A[j + k * C::kLd], A[i + j * C::kLd]);
         }
+        if (tid == 0 && k + 1 < BB) pivot(k + 1);
         __syncthreads();
     }
 
