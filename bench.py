@@ -43,9 +43,9 @@ FP64_FLOP_PER_CYCLE = 152 * 4 * 32 * 2 // 64
 # figure times its units (algorithmic: 1024 B per unit, read + write).
 UPDATE_BYTES_PER_PAIR_ROW = 477.94e6 / (64 * 8192)
 # The same figure for update_split<64> (the tensor-core update, G and V in one
-# launch): ncu, 4096x4096 graded, b = 32, every pair updated, 279.6 MB read +
-# 212.9 MB written for 2 x 64 pairs x 4096 rows.
-SPLIT_UPDATE_BYTES_PER_PAIR_ROW = 492.508e6 / (2 * 64 * 4096)
+# launch): ncu, 4096x4096 graded, b = 32, every pair updated, 279.16 MB read +
+# 209.30 MB written for 2 x 64 pairs x 4096 rows.
+SPLIT_UPDATE_BYTES_PER_PAIR_ROW = 488.461e6 / (2 * 64 * 4096)
 # bf16 digit products per FP64 product in the split contractions (9 slices,
 # levels i + l <= 8)
 SPLIT_PRODUCTS = 45
