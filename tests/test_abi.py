@@ -56,3 +56,29 @@ def test_pivot_table_rejects_bad_orders(lib):
 def test_status_strings(lib):
     for s in range(0, 7):
         assert lib.jsvd_status_string(s)
+
+
+def _struct_fields(name):
+    """Field names of a typedef'd struct in include/jsvd.h, in order."""
+    text = open(os.path.join(ROOT, "include", "jsvd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    return [decl.split()[-1] for decl in body.split(";") if decl.strip()]
+
+
+def test_option_and_info_layouts_match_the_header(lib):
+    """The ctypes structures mirror jsvd_opts / jsvd_info field by field (a
+    missing field would let the library write past the caller's buffer)."""
+    assert [f for f, _ in J.Opts._fields_] == _struct_fields("jsvd_opts")
+    assert [f for f, _ in J.Info._fields_] == _struct_fields("jsvd_info")
+
+
+def test_default_options(lib):
+    import ctypes
+
+    o = J.Opts()
+    lib.jsvd_default_opts(ctypes.byref(o))
+    assert (o.b, o.strategy, o.inner_strategy, o.inner_sweeps, o.max_sweeps, o.precision, o.sort) == \
+        (0, 3, -1, 1, 30, 0, 1)
+    assert o.contraction == 1          # JSVD_CONTRACT_SPLIT: tensor-core contractions by default
+    assert J.make_opts(contraction="fp64").contraction == 0
