@@ -40,6 +40,7 @@ extern "C" {
 #define JSVD_ERR_UNSUPPORTED  5  /* option combination not supported */
 #define JSVD_ERR_TIMEOUT      6  /* a bounded device-side wait gave up */
 #define JSVD_ERR_TOO_LARGE    7  /* jsvd_dgesvj_noalloc: problem exceeds its static scratch */
+#define JSVD_ERR_INTERNAL     8  /* an internal consistency check failed; see jsvd_last_error() */
 
 /* ---- pivot strategies (Sec. 3) ---------------------------------------- */
 #define JSVD_STRAT_MODULUS   0  /* modulus ordering: odd-order modulus completed to even order */
@@ -74,7 +75,8 @@ typedef struct {
     int max_sweeps;      /* limit on block sweeps (0: 30) */
     int precision;       /* JSVD_PREC_* */
     int sort;            /* 1: sigma non-increasing (per sign block for the HSVD) */
-    int contraction;     /* JSVD_CONTRACT_* (default SPLIT); the batched solver always uses FP64 */
+    int contraction;     /* JSVD_CONTRACT_* (default SPLIT); used by every FP64 solver,
+                            the batched one included */
 } jsvd_opts;
 
 typedef struct {
@@ -160,13 +162,14 @@ int jsvd_dgesvj_backward(jsvd_ctx_t ctx, int batch, const int *m, const int *n, 
                          const long long *v_off, const double *dU, const double *dS, const double *dV,
                          double *dA, const long long *a_off);
 
-/* jsvd_dgesvj for callers that cannot allocate device memory (code that runs
- * while a CUDA graph is being captured, a framework whose memory pool owns all
- * device memory, a process under a cudaMalloc cap).  The paper has no
- * counterpart.  Same arguments and results as jsvd_dgesvj, FP64 only
- * (opts->precision must be JSVD_PREC_FP64), without a context: the work runs
- * on `stream` (a cudaStream_t, NULL = legacy default stream) of the current
- * device.
+/* jsvd_dgesvj for callers that cannot allocate device memory (a framework
+ * whose memory pool owns all device memory, a process under a cudaMalloc
+ * cap).  The paper has no counterpart.  Same arguments and results as
+ * jsvd_dgesvj, FP64 only (opts->precision must be JSVD_PREC_FP64), without a
+ * context: the work runs on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) of the current device.  Like jsvd_dgesvj, the call synchronises
+ * that stream once per block sweep (to read the rotation counters) and
+ * before it returns.
  * All scratch lives in one static __device__ array of 64 MiB inside the
  * library, which every GPU that loads the library holds until the process
  * exits; the call makes no cudaMalloc, cudaMallocHost or cudaFree and uses no
@@ -174,7 +177,7 @@ int jsvd_dgesvj_backward(jsvd_ctx_t ctx, int batch, const int *m, const int *n, 
  * problem whose scratch (about 8 * (m+k)*n_pad + 8 * n_pad^2 bytes plus the
  * Gram partials; n_pad = n rounded up to a multiple of 2b) exceeds the array
  * is rejected with JSVD_ERR_TOO_LARGE before any GPU work (m = n = 1024 fits,
- * 2048 does not).
+ * 2048 does not); S, U and V are then left untouched.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call shares the one array and leaves its

@@ -107,6 +107,40 @@ __global__ void k_finalize(const double *__restrict__ G, int ldg, const double *
     }
 }
 
+// Output position of every workspace column (perm[position] = column): the
+// border [ins, ins + k) is skipped; the columns < nplus_w (J = +1) come first,
+// then the others; with `sort` each block is ordered by sigma non-increasing,
+// ties by column index (a stable sort: the rank of column c is the number of
+// block columns that precede it).  A matrix column with support in the border
+// rows breaks an invariant of the bordering: bit 1 of *err is set.
+__global__ void k_sigma_perm(const double *__restrict__ sigma, const int *__restrict__ border, int n_pad, int ins,
+                             int k, int nplus_w, int sort, int *__restrict__ perm,
+                             unsigned long long *__restrict__ err) {
+    __shared__ double s_sig[256];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool real = c < n_pad && !(c >= ins && c < ins + k);
+    const bool pos = c < nplus_w;
+    const double sc = c < n_pad ? sigma[c] : 0.0;
+    int rank = 0;
+    for (int base = 0; base < n_pad; base += 256) {
+        __syncthreads();
+        if (base + (int)threadIdx.x < n_pad) s_sig[threadIdx.x] = sigma[base + threadIdx.x];
+        __syncthreads();
+        if (!real) continue;
+        const int lim = min(256, n_pad - base);
+        for (int t = 0; t < lim; ++t) {
+            const int o = base + t;
+            if ((o >= ins && o < ins + k) || (o < nplus_w) != pos) continue;
+            const double so = s_sig[t];
+            rank += sort ? (so > sc || (so == sc && o < c)) : (o < c);
+        }
+    }
+    if (!real) return;
+    if (border[c]) atomicOr(err, 2ull);
+    // the J = -1 block starts after the nplus_w - k real columns of the J = +1 block
+    perm[(pos ? 0 : nplus_w - k) + rank] = c;
+}
+
 __global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, size_t count) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
         y[e] = (float)x[e];
@@ -216,10 +250,13 @@ int jsvd_ctx::inner_table(int strategy, int BB, const unsigned char **dev) {
             last_error = "no inner pivot table of order " + std::to_string(BB);
             return JSVD_ERR_UNSUPPORTED;
         }
-        std::vector<unsigned char> u(t.begin(), t.end());
+        // the host copy is kept in the context, so it outlives the
+        // stream-ordered copy
+        std::vector<unsigned char> &u = host_inner[BB * 8 + strategy];
+        u.assign(t.begin(), t.end());
         Buffer b;
         if (int r2 = ensure(b, u.size())) return r2;
-        cudaMemcpy(b.ptr, u.data(), u.size(), cudaMemcpyHostToDevice);
+        cudaMemcpyAsync(b.ptr, u.data(), u.size(), cudaMemcpyHostToDevice, stream);
         if (int r3 = check("inner table upload")) return r3;
         it = tables.emplace(key, b).first;
     }
@@ -228,6 +265,14 @@ int jsvd_ctx::inner_table(int strategy, int BB, const unsigned char **dev) {
 }
 
 jsvd_ctx::~jsvd_ctx() {
+    if (owns_memory) release_memory();
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaEvent_t e : ring_events) cudaEventDestroy(e);
+    if (vstream) cudaStreamDestroy(vstream);
+    if (mstream) cudaStreamDestroy(mstream);
+}
+
+void jsvd_ctx::release_memory() {
     for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp, &gexp,
                       &g32, &v32,
                       &tmp_a, &tmp_b, &tmp_g, &b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag,
@@ -238,10 +283,6 @@ jsvd_ctx::~jsvd_ctx() {
     for (auto &kv : tables)
         if (kv.second.ptr) cudaFree(kv.second.ptr);
     if (host_counters) cudaFreeHost(host_counters);
-    for (cudaEvent_t e : events) cudaEventDestroy(e);
-    for (cudaEvent_t e : ring_events) cudaEventDestroy(e);
-    if (vstream) cudaStreamDestroy(vstream);
-    if (mstream) cudaStreamDestroy(mstream);
 }
 
 int jsvd_ctx::ensure_side_stream() {
@@ -606,36 +647,19 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
     double *dsig = (double *)sigma.ptr;
     int *dbd = (int *)border.ptr;
     k_colnorms<<<(n_pad * 32 + 255) / 256, 256, 0, stream>>>(G, g_rows, m_b, m, k, n_pad, dsig, dbd);
-    prof_launches[4] += 2;  // column norms and output assembly
-    if ((rc = check("colnorms"))) return rc;
-    std::vector<double> hs(n_pad);
-    std::vector<int> hb(n_pad);
-    cudaMemcpyAsync(hs.data(), dsig, sizeof(double) * n_pad, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(hb.data(), dbd, sizeof(int) * n_pad, cudaMemcpyDeviceToHost, stream);
-    if ((rc = sync("sigma"))) return rc;
-    std::vector<int> pos, neg;
-    for (int c = 0; c < n_pad; ++c) {
-        if (c >= ins && c < ins + k) continue;   // the border keeps its positions
-        if (hb[c]) {
-            last_error = "a matrix column has support in the border rows";
-            return JSVD_ERR_CUDA;
-        }
-        (c < nplus_w ? pos : neg).push_back(c);
-    }
-    if (o.sort) {
-        auto desc = [&](int x, int y) { return hs[x] > hs[y]; };
-        std::stable_sort(pos.begin(), pos.end(), desc);
-        std::stable_sort(neg.begin(), neg.end(), desc);
-    }
-    std::vector<int> hp(pos);
-    hp.insert(hp.end(), neg.begin(), neg.end());
-    cudaMemcpyAsync(perm.ptr, hp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+    k_sigma_perm<<<(n_pad + 255) / 256, 256, 0, stream>>>(dsig, dbd, n_pad, ins, k, nplus_w, o.sort ? 1 : 0,
+                                                          (int *)perm.ptr, cnt + kCntErr);
     dim3 grid((std::max(m, n) + 255) / 256 < 8 ? (std::max(m, n) + 255) / 256 : 8, n);
     k_finalize<<<grid, 256, 0, stream>>>(G, g_rows, V, v_rows, dsig, (int *)perm.ptr, m, n, ins, k,
                                          nplus, hyperbolic ? 1 : 0, S, U, ldu, Vout, ldv);
+    prof_launches[4] += 3;  // column norms, ordering, output assembly
     if ((rc = check("finalize"))) return rc;
-    // the host vector hp must outlive the async copy
+    cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize, cudaMemcpyDeviceToHost, stream);
     if ((rc = sync("finalize"))) return rc;
+    if (host_counters[kCntErr] & 2ull) {
+        last_error = "a matrix column has support in the border rows";
+        return JSVD_ERR_INTERNAL;
+    }
     if (info) *info = inf;
     return converged ? JSVD_SUCCESS : JSVD_NOT_CONVERGED;
 }
@@ -722,6 +746,7 @@ const char *jsvd_status_string(int s) {
         case JSVD_ERR_UNSUPPORTED: return "unsupported option";
         case JSVD_ERR_TIMEOUT: return "bounded device wait gave up";
         case JSVD_ERR_TOO_LARGE: return "problem exceeds the static scratch of the no-allocation entry point";
+        case JSVD_ERR_INTERNAL: return "internal consistency check failed";
         default: return s < 0 ? "invalid argument" : "unknown status";
     }
 }

@@ -18,6 +18,9 @@ struct jsvd_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool verbose = false;
+    // false when every Buffer points into memory the context does not own
+    // (the no-allocation entry point): nothing is then freed on destruction
+    bool owns_memory = true;
     std::string last_error;
 
     // workspace (grown on demand, freed with the context)
@@ -30,6 +33,7 @@ struct jsvd_ctx {
     unsigned long long *host_counters = nullptr;  // pinned
     std::map<std::pair<int, int>, Buffer> tables;  // (strategy, order) -> device table
     std::map<std::pair<int, int>, std::vector<int>> host_tables;
+    std::map<int, std::vector<unsigned char>> host_inner;  // inner tables (source of their async upload)
 
     // instrumentation (jsvd_profile)
     bool profiling = false;
@@ -51,6 +55,7 @@ struct jsvd_ctx {
     int ensure_side_stream();
 
     virtual ~jsvd_ctx();
+    void release_memory();   // cudaFree / cudaFreeHost of every Buffer, table and the pinned counters
     void set_error(const char *where, cudaError_t e);
     int check(const char *where);
     int sync(const char *where);

@@ -1,8 +1,9 @@
 // jsvd_dgesvj_noalloc: the FP64 SVD for callers that cannot allocate device
-// memory -- code running while a CUDA graph is being captured, inside a
-// framework whose memory pool owns every device byte, or under a cap on
-// cudaMalloc.  The paper has no counterpart; this only changes where the
-// solver's scratch lives.
+// memory -- code inside a framework whose memory pool owns every device byte,
+// or a process under a cap on cudaMalloc.  The paper has no counterpart; this
+// only changes where the solver's scratch lives.  Like jsvd_dgesvj it
+// synchronises its stream (once per block sweep, to read the rotation
+// counters, and once at the end).
 //
 // All scratch (the bordered working copy of G, V, the Gram partials, V', the
 // counters, the pivot tables, the singular-value workspace) is carved from
@@ -38,6 +39,7 @@ struct NoallocCtx : jsvd_ctx {
     explicit NoallocCtx(void *b) : base(static_cast<unsigned char *>(b)) {
         host_counters = counters_host;
         side_streams = false;
+        owns_memory = false;   // every Buffer points into the static array
     }
 
     int ensure(Buffer &buf, size_t bytes) override {
@@ -51,22 +53,6 @@ struct NoallocCtx : jsvd_ctx {
         buf.bytes = bytes;
         used = off + bytes;
         return 0;
-    }
-
-    ~NoallocCtx() override {
-        // nothing was allocated: detach the carved buffers so that the base
-        // destructor frees nothing
-        for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp, &gexp,
-                          &g32, &v32, &tmp_a,
-                          &tmp_b, &tmp_g, &b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag, &b_tab, &b_cnt,
-                          &b_stat, &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &b_bsl, &b_bex, &b_dex,
-                          &b_gexp, &adj_w, &adj_meta,
-                          &adj_desc}) {
-            b->ptr = nullptr;
-            b->bytes = 0;
-        }
-        tables.clear();
-        host_counters = nullptr;
     }
 };
 

@@ -16,6 +16,10 @@ Recipes:
   loguniform_sorted(n, lo, hi, min_gap)  log-uniform values sorted
                               non-increasingly with relative gaps >= min_gap.
   batch_shapes(count)         m ~ U{16..512}, n ~ U{8..m}.
+  graded_columns(m, n, decades)  N(0,1) entries, column j scaled by
+                              10^(-decades j/(n-1)) (no two norms nearly tie).
+  duplicated_pm1_column(A, j0, j1, count)  column j0 := `count` entries +-1
+                              (the rest 0), column j1 := column j0.
 """
 
 from __future__ import annotations
@@ -124,3 +128,21 @@ def workload_batch(count: int = 4096, seed=0, m_hi: int = 512):
         ws.append(rng.standard_normal(int(n)))
         Cs.append(np.asfortranarray(rng.standard_normal((int(m), int(n)))))
     return mats, sig, ws, Cs
+
+
+def graded_columns(m: int, n: int, decades: float = 4.0, seed=0) -> np.ndarray:
+    rng = rng_of(seed)
+    scale = 10.0 ** (-decades * np.arange(n) / max(n - 1, 1))
+    return np.asfortranarray(rng.standard_normal((m, n)) * scale[None, :])
+
+
+def duplicated_pm1_column(A, j0: int, j1: int, count: int = 16, seed=0) -> np.ndarray:
+    """A copy of A whose column j0 holds `count` entries +-1 at random rows
+    (zeros elsewhere) and whose column j1 is an exact copy of column j0."""
+    rng = rng_of(seed)
+    B = np.array(A, dtype=np.float64, order="F", copy=True)
+    B[:, j0] = 0.0
+    rows = rng.choice(B.shape[0], count, replace=False)
+    B[rows, j0] = rng.choice([-1.0, 1.0], count)
+    B[:, j1] = B[:, j0]
+    return np.asfortranarray(B)

@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 CONTRACTIONS = {"fp64": 0, "split": 1}
 STATUS = {0: "success", 1: "not converged", 2: "non-finite input", 3: "CUDA error",
           4: "allocation failed", 5: "unsupported", 6: "device wait timed out",
-          7: "too large for the no-allocation entry point"}
+          7: "too large for the no-allocation entry point", 8: "internal consistency check failed"}
 
 
 class JsvdError(RuntimeError):

@@ -74,10 +74,25 @@ def test_block_sweeps_elementwise(cuda, b, sweeps, contraction):
                           return_info=True, contraction=contraction)
     assert info["sweeps"] == sweeps
     G = _np(U) * _np(S)[None, :]
-    scale = np.linalg.norm(A, 2)
-    assert np.max(np.abs(G - r["G"])) <= 1e-12 * scale
+    assert_columns_close(G, r["G"])
     assert np.max(np.abs(_np(V) - r["V"])) <= 1e-12
     assert info["breakdowns"] == r["breakdowns"] == 0
+
+
+def assert_columns_close(G, Go, rtol=1e-12, zero_tol=None):
+    """Per column: max_i |G_ij - Go_ij| <= rtol ||go_j||.  A column the
+    oracle leaves numerically zero (||go_j|| <= zero_tol, if given) must be
+    numerically zero on the GPU too; an exactly zero oracle column must be
+    exactly zero."""
+    cn = np.linalg.norm(Go, axis=0)
+    for j in range(Go.shape[1]):
+        d = np.max(np.abs(G[:, j] - Go[:, j]))
+        if cn[j] == 0.0:
+            assert d == 0.0, f"column {j}: oracle column is zero, GPU differs by {d:.3e}"
+        elif zero_tol is not None and cn[j] <= zero_tol:
+            assert np.linalg.norm(G[:, j]) <= zero_tol, f"column {j}: not numerically zero"
+        else:
+            assert d <= rtol * cn[j], f"column {j}: |dG| = {d:.3e} > {rtol:.0e} * {cn[j]:.3e}"
 
 
 def smoothed_floor(So, So2, decades=0.5):

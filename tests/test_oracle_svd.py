@@ -155,3 +155,46 @@ def test_block_method_with_identity_border(mn):
     assert np.max(np.abs(s - sl)) <= 50 * np.sqrt(max(n, 2)) * EPS * sl[0]
     assert np.all(r["G"][m:, keep] == 0.0)
     assert np.array_equal(r["G"][:, ~keep], B[:, ~keep])     # the border never moves
+
+
+@pytest.mark.parametrize("b", [4, 8])
+def test_block_method_zero_column_breaks_down_every_pstep(b):
+    """Sec. 4.1 with a singular pivot Gram: a zero column has a zero Gram row,
+    so its Cholesky pivot is exactly 0 in every p-step (one pivot pair per
+    p-step holds it); it stays exactly zero and its singular value is 0."""
+    m, n = 96, 8 * b
+    A = I.graded_columns(m, n, 3.0, seed=b)
+    A[:, 3] = 0.0
+    for sweeps in (1, 2):
+        r = O.block_svd(A, b, strategy="rR", max_sweeps=sweeps)
+        assert r["breakdowns"] == (n // b - 1) * sweeps
+        assert np.all(r["G"][:, np.linalg.norm(r["G"], axis=0) == 0.0] == 0.0)
+    r = O.block_svd(A, b, strategy="rR", max_sweeps=30)
+    assert r["converged"]
+    s = np.sort(O.colnorms(r["G"]))[::-1]
+    assert s[-1] == 0.0
+    sl = np.linalg.svd(A, compute_uv=False)
+    assert np.max(np.abs(s - sl)) <= 100 * np.sqrt(n) * EPS * sl[0]
+    assert _orth(r["V"]) <= 50 * n * EPS
+
+
+@pytest.mark.parametrize("b", [4, 8])
+def test_block_method_duplicate_column_exact_breakdown(b):
+    """An exact duplicate of a column with 16 entries +-1 at pivot position 0:
+    L(0,0) = sqrt(16) = 4 and every multiplier of the copy is exact, so its
+    pivot is exactly 16 - 4^2 = 0 (one breakdown in the first p-step).  The
+    converged result has a numerically zero singular value and otherwise
+    matches LAPACK normwise; the pointwise method agrees."""
+    m, n = 96, 2 * b
+    A = I.duplicated_pm1_column(I.graded_columns(m, n, 3.0, seed=10 + b), 0, 3, seed=b)
+    r1 = O.block_svd(A, b, strategy="rR", max_sweeps=1)
+    assert r1["breakdowns"] == 1
+    r = O.block_svd(A, b, strategy="rR", max_sweeps=30)
+    assert r["converged"]
+    s = np.sort(O.colnorms(r["G"]))[::-1]
+    sl = np.linalg.svd(A, compute_uv=False)
+    assert s[-1] <= 50 * n * EPS * s[0]
+    assert np.max(np.abs(s - sl)) <= 100 * np.sqrt(n) * EPS * sl[0]
+    _, sp, _, _ = O.svd(A)
+    assert sp[-1] <= 50 * n * EPS * sp[0]
+    assert np.max(np.abs(sp - sl)) <= 100 * np.sqrt(n) * EPS * sl[0]

@@ -28,20 +28,23 @@ def lib(cuda):
     return J.library()
 
 
-def _noalloc(lib, A, b):
-    """Call jsvd_dgesvj_noalloc through ctypes on torch-owned buffers."""
+def _noalloc(lib, A, b, want_v=True, want_info=True, S=None):
+    """Call jsvd_dgesvj_noalloc through ctypes on torch-owned buffers, on
+    torch's current stream."""
     m, n = A.shape
     Ac = A.t().contiguous()                              # column-major m x n, ld = m
     U = torch.empty((n, m), dtype=torch.float64, device=A.device)
-    S = torch.empty(n, dtype=torch.float64, device=A.device)
-    V = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    if S is None:
+        S = torch.empty(n, dtype=torch.float64, device=A.device)
+    V = torch.empty((n, n), dtype=torch.float64, device=A.device) if want_v else None
     opts = J.make_opts(b=b)
     info = J.Info()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rc = lib.jsvd_dgesvj_noalloc(m, n, Ac.data_ptr(), m, S.data_ptr(), U.data_ptr(), m, V.data_ptr(), n,
-                                 ctypes.byref(opts), ctypes.byref(info), stream)
-    torch.cuda.synchronize()
-    return rc, U.t(), S, V.t(), info
+    rc = lib.jsvd_dgesvj_noalloc(m, n, Ac.data_ptr(), m, S.data_ptr(), U.data_ptr(), m,
+                                 V.data_ptr() if want_v else None, n, ctypes.byref(opts),
+                                 ctypes.byref(info) if want_info else None, stream)
+    torch.cuda.current_stream().synchronize()
+    return rc, U.t(), S, (V.t() if want_v else None), info
 
 
 def test_no_alloc_matches_regular_entry_point_twice(lib, cuda):
@@ -60,8 +63,25 @@ def test_no_alloc_matches_regular_entry_point_twice(lib, cuda):
         assert float((V.t() @ V - eye).abs().max()) <= 50 * n * EPS
 
 
+def test_no_alloc_partial_svd_on_a_side_stream(lib, cuda):
+    """V = NULL (no right vectors: no V workspace is carved, so the scratch
+    layout differs) and info = NULL, issued on a non-default stream."""
+    m, n, b = 360, 240, 16
+    A = torch.from_numpy(np.ascontiguousarray(I.graded_gaussian(m, n, seed=21))).to(cuda)
+    U1, S1, V1 = J.svd(A, b=b)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        rc, U, S, V, _ = _noalloc(lib, A, b, want_v=False, want_info=False)
+    assert rc == 0 and V is None
+    assert float((S - S1).abs().max()) <= 1e-12 * float(S1[0])
+    assert float((U - U1).abs().max()) <= 1e-12
+
+
 def test_no_alloc_rejects_a_problem_beyond_its_scratch(lib, cuda):
     A = torch.zeros((2048, 2048), dtype=torch.float64, device=cuda)
-    rc, U, S, V, info = _noalloc(lib, A, 16)
+    S = torch.full((2048,), -7.25, dtype=torch.float64, device=cuda)     # sentinel
+    rc, U, S, V, info = _noalloc(lib, A, 16, S=S)
     assert rc == 7                                        # JSVD_ERR_TOO_LARGE
     assert lib.jsvd_status_string(rc)
+    assert bool(torch.all(S == -7.25))                    # outputs untouched
