@@ -8,8 +8,14 @@ generator.  Only tests/, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline / reference legs may import this package.  The product path
 never does.
 
-Numerics are FP64 in plain C (``jacobi_oracle.c``, compiled with
-``-ffp-contract=off``); pivot strategies are plain Python (``pivots.py``).
+Numerics are plain C (``jacobi_oracle.c``, compiled with
+``-ffp-contract=off``), written once over a scalar type and built twice: FP64
+(the parity reference and the timed CPU baseline) and IEEE binary128
+(``q_svd``, ``q_loss_fd``: ground truth for small sizes and finite
+differences of the SVD).  The pairs of one p-step are disjoint, so the C code
+may run them on several threads (``set_threads``); results are bitwise
+identical for any thread count.  Pivot strategies are plain Python
+(``pivots.py``).
 
 Pins (tests/test_oracle_*.py): closed-form 2x2 rotations, Table B.1 of the
 paper (statistical, exact rational arithmetic), Lemma 3.2 and the n = 4
@@ -34,21 +40,24 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "jacobi_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libjacobi_oracle.so")
+_SO_Q = os.path.join(_BUILD, "libjacobi_oracle_q.so")
 _lock = threading.Lock()
 _lib = None
+_lib_q = None
 
 EPS = 2.0 ** -53
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle's C file with gcc (plain C, no fused multiply-add
-    contraction) into oracle/_build/."""
+    contraction) into oracle/_build/: the FP64 library and the binary128 one."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
+    for so, extra in ((_SO, []), (_SO_Q, ["-DJO_QUAD"])):
+        if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+            tmp = so + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", *extra,
+                                   "-fPIC", "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"])
+            os.replace(tmp, so)
     return _SO
 
 
@@ -66,8 +75,30 @@ def _load():
             lib.jo_block_svd.argtypes = [I, I, I, I, P, I, P, I, P, I, I, P, I, I, I, I, P, P]
             lib.jo_colnorms.argtypes = [I, I, P, I, P]
             lib.jo_svd_adjoint.argtypes = [I, I, P, P, P, P, P, P, P]
+            lib.jo_set_threads.argtypes = [I]
             _lib = lib
     return _lib
+
+
+def _load_q():
+    global _lib_q
+    _load()
+    with _lock:
+        if _lib_q is None:
+            lib = ctypes.CDLL(_SO_Q)
+            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            lib.jo_q_set_threads.argtypes = [I]
+            lib.jo_q_svd.argtypes = [I, I, P, I, P, I, I, I, P, P, P, P]
+            lib.jo_q_loss_fd.argtypes = [I, I, P, P, D, P, P, P, I, I, I, P]
+            lib.jo_q_loss_fd.restype = D
+            _lib_q = lib
+    return _lib_q
+
+
+def set_threads(threads: int) -> None:
+    """Worker threads over the disjoint pairs of a p-step (both builds)."""
+    _load().jo_set_threads(int(threads))
+    _load_q().jo_q_set_threads(int(threads))
 
 
 def _ptr(a: np.ndarray):
@@ -120,6 +151,45 @@ def hestenes(A, strategy: str = "rR", nplus: int | None = None, max_sweeps: int 
     return dict(G=G, V=V, sweeps=int(stats[0]), converged=bool(stats[1]),
                 rotations=int(stats[2]), proper=int(stats[3]), swaps=int(stats[4]),
                 rotations_per_sweep=per[: stats[0]].copy())
+
+
+def _pointwise_table(strategy: str, n: int) -> np.ndarray:
+    """The p-strategy table of order n for the pointwise method; odd n uses
+    the order-(n+1) table without the pairs that hold the phantom index n."""
+    if n % 2:
+        full = pivots.strategy(strategy, n + 1)
+        return np.ascontiguousarray(pivots.to_array([[p for p in st if p[1] < n] for st in full]))
+    return np.ascontiguousarray(strategy_array(strategy, n))
+
+
+def q_svd(A, strategy: str = "rR", max_sweeps: int = 100, with_vectors: bool = True):
+    """The pointwise one-sided Jacobi SVD in binary128 (eps = 2^-113), sorted;
+    returns (U, S, V, converged) rounded to double (U, V None unless asked)."""
+    A = _fortran(A)
+    m, n = A.shape
+    tab = _pointwise_table(strategy, n)
+    S = np.empty(n)
+    U = np.asfortranarray(np.empty((m, n))) if with_vectors else None
+    V = np.asfortranarray(np.empty((n, n))) if with_vectors else None
+    st = np.zeros(2, dtype=np.int64)
+    _load_q().jo_q_svd(m, n, _ptr(A), m, _ptr(tab), tab.shape[0], tab.shape[1], max_sweeps, _ptr(S),
+                       _ptr(U) if U is not None else None, _ptr(V) if V is not None else None, _ptr(st))
+    return U, S, V, bool(st[1])
+
+
+def q_loss_fd(A, E, h: float, w, C, strategy: str = "rR", max_sweeps: int = 100) -> float:
+    """Central difference (L(A + hE) - L(A - hE)) / 2h in binary128 of
+    L = sum_i w_i s_i + <C, U V^T> (the loss of the batched adjoint check)."""
+    A, E, C = _fortran(A), _fortran(E), _fortran(C)
+    m, n = A.shape
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    tab = _pointwise_table(strategy, n)
+    ok = ctypes.c_int(0)
+    v = _load_q().jo_q_loss_fd(m, n, _ptr(A), _ptr(E), float(h), _ptr(w), _ptr(C), _ptr(tab), tab.shape[0],
+                               tab.shape[1], max_sweeps, ctypes.byref(ok))
+    if not ok.value:
+        raise RuntimeError("binary128 SVD hit the sweep limit")
+    return v
 
 
 def colnorms(G) -> np.ndarray:
