@@ -46,9 +46,15 @@ UPDATE_BYTES_PER_PAIR_ROW = 477.94e6 / (64 * 8192)
 # launch): ncu, 4096x4096 graded, b = 32, every pair updated, 279.16 MB read +
 # 209.30 MB written for 2 x 64 pairs x 4096 rows.
 SPLIT_UPDATE_BYTES_PER_PAIR_ROW = 488.461e6 / (2 * 64 * 4096)
-# bf16 digit products per FP64 product in the split contractions (9 slices,
-# levels i + l <= 8)
+# bf16 digit products per FP64 product in the split contractions: the Gram and
+# the mma.sync update use 9 7-bit slices (levels i + l <= 8: 45 products), the
+# tcgen05 update 8 8-bit slices (levels i + l <= 7: 36 products)
 SPLIT_PRODUCTS = 45
+TC_UPDATE_PRODUCTS = 36
+# dram__bytes_read.sum + dram__bytes_write.sum of one update_tc<64> launch (ncu,
+# 4096x4096 graded, b = 32, first sweep: every pair updated) divided by its
+# (pair, row) units; None until measured for the current kernel
+TC_UPDATE_BYTES_PER_PAIR_ROW = None
 
 WORKLOADS = {
     # name: (m, n, generator, description)
@@ -348,7 +354,7 @@ def run_gpu(args) -> None:
 
     # FP64 peak of this GPU, measured now (warm clocks), for the roofline
     peak_dfma, peak_dmma = J.fp64_peak(seconds=args.peak_seconds)
-    peak_mma = J.bf16_mma_peak(seconds=args.peak_seconds) if args.contraction == "split" else None
+    peak_mma = J.bf16_mma_peak(seconds=args.peak_seconds) if args.contraction in ("split", "split_sync") else None
     torch.cuda.synchronize()
 
     # ---- timed region: K complete SVDs with inputs resident in HBM ------------
@@ -419,7 +425,8 @@ def run_gpu(args) -> None:
     achieved = d_flops / (d_ms * 1e-3) / 1e12 if d_ms > 0 else 0.0
     traffic = None
     bb = 2 * last_b
-    per_row = SPLIT_UPDATE_BYTES_PER_PAIR_ROW if args.contraction == "split" else UPDATE_BYTES_PER_PAIR_ROW
+    per_row = {"split": TC_UPDATE_BYTES_PER_PAIR_ROW, "split_sync": SPLIT_UPDATE_BYTES_PER_PAIR_ROW,
+               "fp64": UPDATE_BYTES_PER_PAIR_ROW}[args.contraction]
     if dom == "update" and d_launch and per_row is not None:
         # ncu DRAM bytes per (pair, row) of the update kernel x the launch's units
         traffic = per_row * (d_flops / (2.0 * bb * bb)) / d_launch
@@ -427,15 +434,18 @@ def run_gpu(args) -> None:
                 f"instruction per 64 cycles, the sm__inst_executed_pipe_fp64 peak) x median SM clock "
                 f"{sm_mhz:.0f} MHz in the timed region; in-run probes: DMMA {peak_dmma:.3f}, DFMA "
                 f"{peak_dfma:.3f} TFLOP/s")
-    if args.contraction == "split" and dom in ("gram", "update"):
-        # tensor-core kernels: each FP64 product is SPLIT_PRODUCTS bf16 digit products
+    if args.contraction in ("split", "split_sync") and dom in ("gram", "update"):
+        # tensor-core kernels: each FP64 product is `products` bf16 digit products
+        products = TC_UPDATE_PRODUCTS if (args.contraction == "split" and dom == "update") else SPLIT_PRODUCTS
         bf16_peak, bf16_src = bf16_peak_tflops(sustained=True)
-        tensor = SPLIT_PRODUCTS * achieved
+        tensor = products * achieved
         roofline = {"bound": "tensor", "achieved": tensor, "peak": bf16_peak, "unit": "TFLOP/s",
                     "frac": tensor / bf16_peak, "traffic": traffic,
-                    "kernel": {"gram": "gram_split", "update": "update_split"}[dom], "launches": d_launch,
+                    "kernel": {"gram": "gram_split",
+                               "update": "update_tc" if args.contraction == "split" else "update_split"}[dom],
+                    "launches": d_launch,
                     "peak_source": bf16_src + " (of measured); achieved = "
-                                   f"{SPLIT_PRODUCTS} bf16 digit products x the kernel's algorithmic FP64 flops / "
+                                   f"{products} bf16 digit products x the kernel's algorithmic FP64 flops / "
                                    "its CUDA-event time",
                     "fp64_equivalent_tflops": achieved,
                     "mma_sync_bf16_peak": peak_mma,
@@ -449,11 +459,13 @@ def run_gpu(args) -> None:
     kernels = {c: {"ms": prof[c][0], "launches": prof[c][1], "tflops": (prof[c][2] / (prof[c][0] * 1e-3) / 1e12)
                    if prof[c][0] > 0 else None, "share": prof[c][0] / ms_total if ms_total else None}
                for c in ("gram", "jacobi", "update", "update_v")}
-    if args.contraction == "split":
-        kernels["update"]["note"] = "update of G and V in one launch (tensor-core split contractions)"
+    if args.contraction in ("split", "split_sync"):
+        kernels["update"]["note"] = ("update of G and V in one launch (tcgen05, 8-bit digits)" if args.contraction ==
+                                     "split" else "update of G and V in one launch (mma.sync, 7-bit digits)")
         for c in ("gram", "update"):
             if kernels[c]["tflops"]:
-                kernels[c]["tensor_tflops"] = SPLIT_PRODUCTS * kernels[c]["tflops"]
+                pr = TC_UPDATE_PRODUCTS if (args.contraction == "split" and c == "update") else SPLIT_PRODUCTS
+                kernels[c]["tensor_tflops"] = pr * kernels[c]["tflops"]
         kernels["update_v"]["note"] = "no side-stream V update with split contractions"
     else:
         kernels["update_v"]["note"] = ("V update on the low-priority side stream: it runs in the main stream's "
@@ -539,8 +551,9 @@ def main():
                    help="block width (default 32; the batched workload autotunes it per bucket of n)")
     p.add_argument("--strategy", default=None, help="pivot strategy (default rR; modulus for small512)")
     p.add_argument("--max-sweeps", type=int, default=30)
-    p.add_argument("--contraction", default="split", choices=["fp64", "split"],
-                   help="FP64 block contractions: FP64 FMA kernels or split bf16 digits on the tensor cores")
+    p.add_argument("--contraction", default="split", choices=["fp64", "split", "split_sync"],
+                   help="FP64 block contractions: FP64 FMA kernels, or split bf16 digits on the tensor cores "
+                        "(split: tcgen05 update; split_sync: mma.sync update)")
     p.add_argument("--inner-sweeps", type=int, default=1,
                    help="inner sweeps per pivot pair: 1 = block-oriented, 30 = full block (Sec. 4.3)")
     p.add_argument("--seed", type=int, default=0)

@@ -55,14 +55,20 @@ extern "C" {
 
 /* ---- how the FP64 block contractions are evaluated ----------------------
  * The Gram matrix of a pivot pair (Eq. (2.7)) and the block update (Eq. (2.9))
- * of the FP64 sweeps.  The paper forms both with FP64 arithmetic.  SPLIT forms
- * them on the bf16 tensor cores from exact 7-bit digit slices of power-of-two
- * scaled fixed-point operands (9 slices, 45 digit products per FP64 product,
- * exact FP32 accumulation, one FP64 rounding per result); with the column
- * scaling it applies its error is at or below that of the FP64 FMA form.
- * Used by jsvd_dgesvj, jsvd_dhsvj and the FP64 stage of the mixed solver. */
-#define JSVD_CONTRACT_FP64   0  /* FP64 FMA kernels */
-#define JSVD_CONTRACT_SPLIT  1  /* split bf16 digits on the tensor cores */
+ * of the FP64 sweeps.  The paper forms both with FP64 arithmetic.  The split
+ * forms evaluate them on the bf16 tensor cores from exact digit slices of
+ * power-of-two scaled fixed-point operands (exact FP32 accumulation of the
+ * digit products, one FP64 rounding per result); with the column scaling they
+ * apply, their error is at or below that of the FP64 FMA form.
+ *   SPLIT:       Gram from 9 7-bit slices (45 products, mma.sync); update on
+ *                tcgen05 with tensor-memory accumulators from 8 8-bit slices
+ *                (36 products) -- the default.
+ *   SPLIT_SYNC:  both from 9 7-bit slices on mma.sync.
+ * Used by jsvd_dgesvj, jsvd_dhsvj and the FP64 stage of the mixed solver; the
+ * batched solver runs the mma.sync forms for both split modes. */
+#define JSVD_CONTRACT_FP64        0  /* FP64 FMA kernels */
+#define JSVD_CONTRACT_SPLIT       1  /* split digits; tcgen05 update */
+#define JSVD_CONTRACT_SPLIT_SYNC  2  /* split digits; mma.sync update */
 
 typedef struct jsvd_ctx *jsvd_ctx_t;
 
@@ -75,8 +81,7 @@ typedef struct {
     int max_sweeps;      /* limit on block sweeps (0: 30) */
     int precision;       /* JSVD_PREC_* */
     int sort;            /* 1: sigma non-increasing (per sign block for the HSVD) */
-    int contraction;     /* JSVD_CONTRACT_* (default SPLIT); used by every FP64 solver,
-                            the batched one included */
+    int contraction;     /* JSVD_CONTRACT_* (default SPLIT); used by every FP64 solver */
 } jsvd_opts;
 
 typedef struct {

@@ -410,7 +410,9 @@ int jsvd_ctx::solve_batched(int batch, const int *m, const int *n, const int *bs
         return JSVD_ERR_UNSUPPORTED;
     }
     int rc;
-    const bool split = o.contraction == JSVD_CONTRACT_SPLIT;
+    // the batched solver's split contractions are the mma.sync forms for both
+    // split modes
+    const bool split = o.contraction == JSVD_CONTRACT_SPLIT || o.contraction == JSVD_CONTRACT_SPLIT_SYNC;
     // ---- per-matrix layout ---------------------------------------------------
     std::vector<BMat> mats(batch);
     std::vector<int> tables;

@@ -410,7 +410,8 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         last_error = "unknown precision mode";
         return JSVD_ERR_UNSUPPORTED;
     }
-    if (o.contraction != JSVD_CONTRACT_FP64 && o.contraction != JSVD_CONTRACT_SPLIT) {
+    if (o.contraction != JSVD_CONTRACT_FP64 && o.contraction != JSVD_CONTRACT_SPLIT &&
+        o.contraction != JSVD_CONTRACT_SPLIT_SYNC) {
         last_error = "unknown contraction mode";
         return JSVD_ERR_UNSUPPORTED;
     }
@@ -447,7 +448,9 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
     // than the overlap gained (measured on every workload but the 8192^2 one,
     // where the two were within 2 %).  The FP64 FMA form overlaps the V update
     // on the side stream.
-    const bool split = o.contraction == JSVD_CONTRACT_SPLIT;
+    const bool split = o.contraction == JSVD_CONTRACT_SPLIT || o.contraction == JSVD_CONTRACT_SPLIT_SYNC;
+    // the tcgen05 update (8-bit digit images) or the mma.sync one (7-bit)
+    const bool tc = o.contraction == JSVD_CONTRACT_SPLIT;
     const size_t bsl_pairs = (size_t)npairs * 2 * (size_t)split_b_elems_rt(BB);
     if (split) {
         if ((rc = ensure(bslice, sizeof(uint16_t) * bsl_pairs))) return rc;
@@ -604,6 +607,10 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
                 fprintf(stderr, "[jsvd] %s sweep %d: rotations %llu proper %llu updated %llu off %.3e\n",
                         a.fp32 ? "fp32" : "fp64", *done, host_counters[kCntRot], host_counters[kCntProper],
                         host_counters[kCntUpdated], off);
+            if (host_counters[kCntErr] & 4ull) {
+                last_error = "a bounded wait of the tensor-core update gave up";
+                return JSVD_ERR_TIMEOUT;
+            }
             if (host_counters[kCntProper] == 0) { *conv = 1; break; }
             if (*done == 1) first_proper = host_counters[kCntProper];
             if (stop_frac > 0.0 && (double)host_counters[kCntProper] < stop_frac * (double)first_proper) break;
@@ -630,7 +637,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         // Stage 2: Q = polar factor of V32 in FP64, G := G Q, V := Q.
         if ((rc = polar_and_apply(G, g_rows, n_pad, nplus_w, V32, v_rows, V, v_rows))) return rc;
     }
-    a.G = G; a.V = want_v ? V : nullptr; a.fp32 = 0; a.eps = kEps; a.split = split ? 1 : 0;
+    a.G = G; a.V = want_v ? V : nullptr; a.fp32 = 0; a.eps = kEps; a.split = split ? 1 : 0; a.tc = tc ? 1 : 0;
     if (split) {
         // Gram partials of 256 rows; column exponent bounds of the current G
         a.g_chunks = g_rows / kGramRowsSplit;

@@ -1,0 +1,256 @@
+// The 8-bit digit form of the FP64-accurate block update on tcgen05
+// (Eq. (2.9): [A_P A_Q] := [A_P A_Q] V').
+//
+// Same fixed point as the 7-bit form (split_mma.cuh): every row of the left
+// operand and every column of the right one gets a power-of-two scale 2^E
+// with |x| < 2^E and becomes Y = trunc(x 2^(62-E)), |Y| < 2^62.  Y is written
+// in balanced base 256 with 8 digits d_0..d_7 in [-128, 127]:
+// Z = Y + 0x8080808080808080 (all bytes biased by 128), d_i = byte(7-i) - 128,
+// Y = sum_i d_i 256^(7-i); every digit is an exact bf16.  A product sum
+//   sum_j Y_A Y_B = 2^56 T,  T = sum_{L<=7} lev_L 256^(7-L),
+//   lev_L = sum_{i+l=L} sum_j a_i(j) b_l(j),
+// keeps the 36 digit products with i + l <= 7 (the dropped ones are below
+// 2^-59 of the scale product).  For a contraction of length K <= 64 every
+// level sum is an integer of magnitude <= 8 * 64 * 128^2 = 2^23, so FP32
+// accumulation in the tensor cores is exact; the 8 level accumulators of 64
+// output columns fill the 512 TMEM columns exactly (9 levels of the 7-bit
+// form would not fit).  T is recombined in integers and rounded once to FP64;
+// the result is T 2^(E_A + E_B - 68).
+//
+// Right-factor image (written by the per-pair Jacobi kernel, copied whole
+// into shared memory by the update kernel): for output-column half h (of NH,
+// NC = BB / NH columns each) and K-step ks (16 inputs) a block of 8 * NC
+// rows -- slice l's rows l*NC .. l*NC + NC - 1 hold output columns
+// h*NC .. h*NC + NC - 1 -- of 16 bf16 each, in the no-swizzle K-major
+// core-matrix layout of tc_umma.cuh; blocks ordered (ks, h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "split_mma.cuh"
+#include "tc_umma.cuh"
+
+namespace jsvd {
+namespace split8 {
+
+constexpr int kSlices = 8;
+constexpr unsigned long long kBias = 0x8080808080808080ull;
+
+template <int BB> struct TcCfg {
+    static constexpr int kKS = BB / 16;                 // K-steps of 16
+    static constexpr int kNH = BB == 64 ? 2 : 1;        // output-column halves
+    static constexpr int kNC = BB / kNH;                // columns per half: 32, 32, 16
+    static constexpr int kDW = kSlices * kNC;           // TMEM columns of one accumulator set
+    static constexpr int kTmemCols = 2 * kDW;           // two sets: 512, 512, 256
+    static constexpr int kBBlock = kSlices * kNC * 32;  // bytes of one (ks, h) block
+    static constexpr int kBBytes = kKS * kNH * kBBlock; // 16 BB^2
+};
+
+// bf16 elements of one version of a pair's right-factor image.
+template <int BB>
+constexpr int image_elems() { return TcCfg<BB>::kBBytes / 2; }
+
+// Z = kBias + trunc(x 2^(off + 62 - E)), given |x 2^off| < 2^E.
+__device__ __forceinline__ unsigned long long fixed_biased(double x, int off, int E) {
+    const long long bits = __double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = (unsigned long long)bits & 0x000fffffffffffffull;
+    int ex = -1022;
+    if (ef) {
+        mant |= 0x0010000000000000ull;
+        ex = ef - 1023;
+    }
+    const int sh = ex + off - E + 10;    // <= 9 because |x 2^off| < 2^E
+    unsigned long long y;
+    if (sh >= 0)
+        y = mant << sh;
+    else
+        y = sh > -64 ? (mant >> (-sh)) : 0ull;
+    return bits < 0 ? kBias - y : kBias + y;
+}
+
+// Digit I (0 = most significant) of z as an FP32 value: the byte is placed
+// under the exponent of 2^23 (0x4B0000uu = 2^23 + u) and 2^23 + 128 is
+// subtracted, both exact.
+template <int I>
+__device__ __forceinline__ float digit_f32(unsigned long long z) {
+    constexpr int byte = 7 - I;
+    const uint32_t w = byte >= 4 ? (uint32_t)(z >> 32) : (uint32_t)z;
+    const uint32_t f = __byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(byte & 3));
+    return __fsub_rn(__uint_as_float(f), 8388736.0f);
+}
+
+// Digits I of z0 (low half) and z1 (high half) as one bf16x2 word (exact).
+template <int I>
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long z0, unsigned long long z1) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(digit_f32<I>(z1)), "f"(digit_f32<I>(z0)));
+    return d;
+}
+
+// The 8 slices of 8 consecutive K entries z[0..7] (one 16-byte row chunk of a
+// core matrix per slice): dst points at slice 0's chunk, slices slice_stride
+// bytes apart.
+__device__ __forceinline__ void store_digits8(unsigned char *dst, int slice_stride, const unsigned long long (&z)[8]) {
+#define JSVD_S8(I)                                                                                          \
+    *reinterpret_cast<uint4 *>(dst + (I) * slice_stride) =                                                  \
+        make_uint4(digit_pair<I>(z[0], z[1]), digit_pair<I>(z[2], z[3]), digit_pair<I>(z[4], z[5]),      \
+                   digit_pair<I>(z[6], z[7]));
+    JSVD_S8(0) JSVD_S8(1) JSVD_S8(2) JSVD_S8(3) JSVD_S8(4) JSVD_S8(5) JSVD_S8(6) JSVD_S8(7)
+#undef JSVD_S8
+}
+
+// The FP64 value 2^(e - 68) * T, T = sum_L lev[L] 256^(7-L), rounded once to
+// nearest (ties to even), in 64-bit integer arithmetic.  Level values are
+// exact integers, |lev| <= 2^23, so T = hi 2^32 + lo with |hi|, |lo| < 2^48;
+// |T| is brought to the form M 2^32 + R (0 <= R < 2^32, M < 2^48), whose
+// leading 64 bits are rounded to 53.
+__device__ __forceinline__ double combine(const float (&lv)[kSlices], int e) {
+    long long v[kSlices];
+#pragma unroll
+    for (int L = 0; L < kSlices; ++L)
+        v[L] = (long long)(__float_as_int(__fadd_rn(lv[L], 12582912.0f)) - 0x4B400000);
+    const long long hi = v[0] * 16777216ll + v[1] * 65536ll + v[2] * 256ll + v[3];
+    const long long lo = v[4] * 16777216ll + v[5] * 65536ll + v[6] * 256ll + v[7];
+    // T = H 2^32 + L, 0 <= L < 2^32 (floor division of lo by 2^32)
+    const long long H = hi + (lo >> 32);
+    const uint32_t L = (uint32_t)(unsigned long long)lo;
+    const bool neg = H < 0;
+    unsigned long long M;
+    uint32_t R;
+    if (!neg) {
+        M = (unsigned long long)H;
+        R = L;
+    } else if (L != 0u) {            // -T = (-H - 1) 2^32 + (2^32 - L)
+        M = (unsigned long long)(-H - 1);
+        R = 0u - L;
+    } else {
+        M = (unsigned long long)(-H);
+        R = 0u;
+    }
+    unsigned long long mant;
+    int ex;                          // |T| = mant 2^(ex - 52), mant in [2^52, 2^53)
+    if (M == 0ull) {
+        if (R == 0u) return 0.0;
+        const int p = 31 - __clz((int)R);    // exact: at most 32 significant bits
+        mant = (unsigned long long)R << (52 - p);
+        ex = p;
+    } else {
+        const int s = __clzll((long long)M);  // 16 .. 63
+        unsigned long long top;              // leading one at bit 63
+        bool sticky;
+        if (s < 32) {
+            top = (M << s) | (unsigned long long)(R >> (32 - s));
+            sticky = (uint32_t)(R << s) != 0u;
+        } else {
+            top = (M << s) | ((unsigned long long)R << (s - 32));
+            sticky = false;
+        }
+        ex = 95 - s;
+        mant = top >> 11;
+        const uint32_t rem = (uint32_t)top & 0x7ffu;
+        if (rem > 0x400u || (rem == 0x400u && (sticky || (mant & 1ull)))) ++mant;
+        if (mant >> 53) {
+            mant >>= 1;
+            ++ex;
+        }
+    }
+    const int be = ex + e - 68 + 1023;
+    const unsigned long long sign = (unsigned long long)neg << 63;
+    if (be >= 1 && be <= 2046)
+        return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0x000fffffffffffffull)));
+    // rare: the result is outside the normal range; +-mant is exact
+    const double r = __longlong_as_double((long long)(sign | (1075ull << 52) | (mant & 0x000fffffffffffffull)));
+    return split::scale_slow(r, ex - 52 + e - 68);
+}
+
+// The same value as combine(), computed with 32-bit integer operations only
+// and without data-dependent branches (so that the compiler can interleave
+// the recombination of several outputs): the levels are carry-propagated
+// into bytes,
+//   T = D0 2^56 + F,  F = d1 d2 ... d7 (bytes, 0 <= F < 2^56),
+// |T| is shifted left by whole words and then bits until its leading one is
+// at bit 95 of a 96-bit value, and rounded once to 53 bits, ties to even.
+__device__ __forceinline__ double combine32(const float (&lv)[kSlices], int e) {
+    int l[kSlices];
+#pragma unroll
+    for (int L = 0; L < kSlices; ++L) l[L] = __float_as_int(__fadd_rn(lv[L], 12582912.0f)) - 0x4B400000;
+    uint32_t d[kSlices];
+    int c = 0;
+#pragma unroll
+    for (int L = kSlices - 1; L >= 1; --L) {
+        const int x = l[L] + c;
+        d[L] = (uint32_t)x & 255u;
+        c = x >> 8;                      // arithmetic: floor division by 256
+    }
+    const int D0 = l[0] + c;             // |D0| < 2^24
+    // F = (Fh << 32) | Fl, Fh = d1 d2 d3 (24 bits), Fl = d4 d5 d6 d7
+    const uint32_t Fl0 = __byte_perm(__byte_perm(d[7], d[6], 0x0040u), __byte_perm(d[5], d[4], 0x0040u), 0x5410u);
+    const uint32_t Fh0 = __byte_perm(__byte_perm(d[3], d[2], 0x0040u), d[1], 0x5410u);
+    // |T| = A 2^56 + Fh 2^32 + Fl; for T < 0 the 80-bit two's complement:
+    // (-D0) 2^56 - F = (-D0 - [F != 0]) 2^56 + (2^56 - F) mod 2^56
+    const bool neg = D0 < 0;
+    const bool zlo = Fl0 == 0u, zf = zlo && Fh0 == 0u;
+    const uint32_t Fl = neg ? 0u - Fl0 : Fl0;
+    const uint32_t Fh = neg ? ((0u - Fh0 - (zlo ? 0u : 1u)) & 0x00ffffffu) : Fh0;
+    const uint32_t A = neg ? (uint32_t)(-D0) - (zf ? 0u : 1u) : (uint32_t)D0;
+    // 96-bit view n2:n1:n0, then whole-word shifts while the top word is zero
+    uint32_t w2 = A >> 8, w1 = (A << 24) | Fh, w0 = Fl;
+    int ex = 95;                         // bit position of the leading one after the shifts
+    const bool s1 = w2 == 0u;
+    w2 = s1 ? w1 : w2; w1 = s1 ? w0 : w1; w0 = s1 ? 0u : w0; ex -= s1 ? 32 : 0;
+    const bool s2 = w2 == 0u;
+    w2 = s2 ? w1 : w2; w1 = s2 ? w0 : w1; w0 = s2 ? 0u : w0; ex -= s2 ? 32 : 0;
+    const bool zero = w2 == 0u;
+    const int z = __clz((int)w2);        // 32 if zero (then the result is 0 below)
+    const uint32_t hi = __funnelshift_l(w1, w2, z), lo = __funnelshift_l(w0, w1, z);
+    const bool sticky = (w0 << (z & 31)) != 0u && z < 32;
+    ex -= z;
+    // mantissa = top 53 bits of hi:lo; the next 11 bits and sticky round it
+    unsigned long long mant = ((unsigned long long)(hi >> 11) << 32) | __funnelshift_r(lo, hi, 11);
+    const uint32_t rem = lo & 0x7ffu;
+    const bool up = rem > 0x400u || (rem == 0x400u && (sticky || (mant & 1ull)));
+    mant += up ? 1ull : 0ull;
+    const bool carry = (mant >> 53) != 0ull;   // rounded up to 2^53
+    mant = carry ? (mant >> 1) : mant;
+    ex += carry ? 1 : 0;
+    const int be = ex + e - 68 + 1023;
+    const uint32_t sign = neg ? 0x80000000u : 0u;
+    const uint32_t mh = (uint32_t)(mant >> 32) & 0x000fffffu, ml = (uint32_t)mant;
+    if (zero) return 0.0;
+    if (be >= 1 && be <= 2046) return __hiloint2double((int)(sign | ((uint32_t)be << 20) | mh), (int)ml);
+    const double r = __hiloint2double((int)(sign | (1075u << 20) | mh), (int)ml);   // +-mant, exact
+    return split::scale_slow(r, ex - 52 + e - 68);
+}
+
+// Right-factor images of one pivot pair (see above): version 0 = D V' for
+// [G_P G_Q] (D = diag(2^dx[j])), version 1 = V' for [V_P V_Q].  W is V' in
+// shared memory (column-major, ld ldw); bexp[ver * BB + k] receives column
+// k's exponent bound F_k.  Executed by NT threads.
+template <int BB, int NT>
+__device__ __forceinline__ void right_factor_image(const double *W, int ldw, const int *dx,
+                                                   uint16_t *__restrict__ img, int *__restrict__ bexp) {
+    using C = TcCfg<BB>;
+    for (int t = threadIdx.x; t < 2 * BB; t += NT) {
+        const int ver = t / BB, k = t % BB;
+        const double *w = W + k * ldw;
+        int F = split::kNoExp;
+        for (int j = 0; j < BB; ++j) F = max(F, split::exp_bound(w[j], ver ? 0 : dx[j]));
+        if (F == split::kNoExp) F = 0;
+        bexp[ver * BB + k] = F;
+        const int h = k / C::kNC, n = k % C::kNC;
+        unsigned char *base = reinterpret_cast<unsigned char *>(img + (size_t)ver * image_elems<BB>());
+        for (int j = 0; j < BB; j += 8) {
+            unsigned long long z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) z[u] = fixed_biased(w[j + u], ver ? 0 : dx[j + u], F);
+            const int ks = j / 16, kk = j % 16;
+            unsigned char *dst = base + (ks * C::kNH + h) * C::kBBlock + tc::op_offset(n, kk);
+            store_digits8(dst, C::kNC * 32, z);
+        }
+    }
+}
+
+}  // namespace split8
+}  // namespace jsvd

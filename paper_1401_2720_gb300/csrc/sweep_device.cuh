@@ -15,6 +15,7 @@
 #include <cstdint>
 
 #include "rotation.cuh"
+#include "split8.cuh"
 #include "split_mma.cuh"
 
 namespace jsvd {
@@ -158,10 +159,13 @@ __device__ __forceinline__ void gram_unit(const T *__restrict__ G, int ldg, int 
 // memory (column-major, ld BB+1).  Column k of a version gets the exponent
 // bound F_k of its entries and the digits of trunc(x 2^(62-F_k)), stored as
 // out[slice][k][j] (K = j contiguous, row stride BB + kPad).
+//
+// With tc the images are those of the tcgen05 update instead: 8 balanced
+// 8-bit digits in its operand layout (split8::right_factor_image).
 template <int BB, int NT = Cfg<BB>::kJacThreads>
 __device__ __forceinline__ void split_right_factor(const double *W, const double *hdiag, int *dx,
                                                    uint16_t *__restrict__ out, int *__restrict__ bexp,
-                                                   int *__restrict__ dexp) {
+                                                   int *__restrict__ dexp, bool tc = false) {
     using C = Cfg<BB>;
     constexpr int LD = BB + split::kPad;
     for (int j = threadIdx.x; j < BB; j += NT) {
@@ -171,6 +175,10 @@ __device__ __forceinline__ void split_right_factor(const double *W, const double
         dexp[j] = d;
     }
     __syncthreads();
+    if (tc) {
+        split8::right_factor_image<BB, NT>(W, C::kLd, dx, out, bexp);
+        return;
+    }
     for (int t = threadIdx.x; t < 2 * BB; t += NT) {
         const int ver = t / BB, k = t % BB;
         const double *w = W + k * C::kLd;
@@ -382,7 +390,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
                                             int *__restrict__ vflag, unsigned long long *__restrict__ counters,
                                             double *smem, uint16_t *__restrict__ bsl = nullptr,
                                             int *__restrict__ bexp = nullptr, int *__restrict__ dexp = nullptr,
-                                            int *__restrict__ gexp = nullptr) {
+                                            int *__restrict__ gexp = nullptr, bool tc = false) {
     using C = Cfg<BB>;
     double *A = smem;
     double *B = smem + BB * C::kLd;
@@ -563,7 +571,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
         vp[e] = (double)Vt[i + j * C::kLd];
     }
     if constexpr (sizeof(RT) == sizeof(double))
-        if (bsl && any_change) split_right_factor<BB, NT>(A, hdiag, dx, bsl, bexp, dexp);
+        if (bsl && any_change) split_right_factor<BB, NT>(A, hdiag, dx, bsl, bexp, dexp, tc);
     // the update of G rewrites these columns and max-reduces their new bounds
     if (gexp && any_change)
         for (int k = tid; k < BB; k += NT) gexp[block_col(P, Q, b, k)] = split::kNoExp;

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(NT) pair_jacobi(PStepArgs a) {
                     a.nplus, a.bord_lo, a.bord_hi, a.inner_sweeps, a.eps, a.vprime + (size_t)pair * BB * BB, a.vflag + pair,
                     a.counters, smem, a.split ? a.bslice + (size_t)pair * 2 * split_b_elems<BB>() : nullptr,
                     a.split ? a.bexp + (size_t)pair * 2 * BB : nullptr, a.split ? a.dexp + (size_t)pair * BB : nullptr,
-                    a.split ? a.gexp : nullptr);
+                    a.split ? a.gexp : nullptr, a.tc != 0);
 }
 
 template <int BB, typename T>

@@ -59,6 +59,8 @@ struct PStepArgs {
     int *bexp;              // [npairs][2][BB] column exponent bounds of the right factors
     int *dexp;              // [npairs][BB] column scales of [G_P G_Q]
     int *gexp;              // [n_pad] exponent bound of every column of G: |g_ij| < 2^gexp[j]
+    int tc;                 // 1: the update runs on tcgen05 (update_tc.cu); bslice then holds the
+                            // 8-bit images [npairs][2][split8::image_elems<BB>]
 };
 
 
@@ -70,6 +72,8 @@ enum class Phase { Gram, Jacobi, UpdateG, UpdateV, UpdateGV };
 void launch_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
 // The tensor-core forms of the Gram and update phases (sweep_split.cu).
 void launch_split_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
+// The tcgen05 block update (update_tc.cu): G and V of every pair with V' != I.
+void launch_update_tc(int BB, const PStepArgs &a, cudaStream_t s);
 // gexp[j] = exponent bound of column j of G (rows [0, rows)), one CTA per column.
 void launch_col_maxexp(const double *G, int ldg, int rows, int ncols, int *gexp, cudaStream_t s);
 

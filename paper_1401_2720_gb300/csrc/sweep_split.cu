@@ -97,6 +97,11 @@ static void launch_split_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
         gram_split<BB><<<dim3(ctas, a.npairs), S::kGThreads, gram_split_smem<BB>(), s>>>(a);
         return;
     }
+    if (a.tc) {
+        // G and V in one persistent tcgen05 launch
+        launch_update_tc(BB, a, s);
+        return;
+    }
     const int gu = (ph == Phase::UpdateV) ? 0 : (a.g_rows + S::kUpdRowsPerCta - 1) / S::kUpdRowsPerCta;
     const int vu = (ph == Phase::UpdateG || !a.V) ? 0 : (a.v_rows + S::kUpdRowsPerCta - 1) / S::kUpdRowsPerCta;
     if (gu + vu > 0)

@@ -83,23 +83,25 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(mbar))
                  : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
+// One try_wait: the thread is suspended (up to about suspend_ns nanoseconds)
+// until the phase with the given parity completes; false if it has not.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity, uint32_t suspend_ns = 0) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(mbar)), "r"(parity)
+        : "r"(smem_addr(mbar)), "r"(parity), "r"(suspend_ns)
         : "memory");
     return ok != 0;
 }
 // Wait for the phase with the given parity to complete; gives up after
-// `limit` polls (each try_wait may itself suspend for a while) and returns
-// false then.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t limit = (1u << 24)) {
+// `limit` suspended polls of at most ~suspend_ns each and returns false then.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t limit = 4096,
+                                          uint32_t suspend_ns = 1000000) {
     for (uint32_t i = 0; i < limit; ++i)
-        if (mbar_try_wait(mbar, parity)) return true;
+        if (mbar_try_wait(mbar, parity, suspend_ns)) return true;
     return false;
 }
 
@@ -116,6 +118,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&r)[2]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 

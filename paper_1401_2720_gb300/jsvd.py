@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libjsvd.so")
 STRATEGIES = {"modulus": 0, "R": 1, "C": 2, "rR": 3, "rC": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 # FP64 block contractions: FP64 FMA kernels, or split bf16 digits on the tensor cores
-CONTRACTIONS = {"fp64": 0, "split": 1}
+CONTRACTIONS = {"fp64": 0, "split": 1, "split_sync": 2}
 STATUS = {0: "success", 1: "not converged", 2: "non-finite input", 3: "CUDA error",
           4: "allocation failed", 5: "unsupported", 6: "device wait timed out",
           7: "too large for the no-allocation entry point", 8: "internal consistency check failed"}

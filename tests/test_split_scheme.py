@@ -1,9 +1,11 @@
 """The arithmetic of the split-digit contractions, modelled exactly on the CPU.
 
-The tensor-core Gram and update form each FP64 product from 9 balanced 7-bit
-digits of power-of-two scaled fixed-point operands, accumulate the 45 digit
-products with i + l <= 8 per level in FP32, and recombine the levels into one
-FP64 number (see the device header that implements it).  This model uses Python
+The tensor-core Gram forms each FP64 product from 9 balanced 7-bit digits of
+power-of-two scaled fixed-point operands and accumulates the 45 digit
+products with i + l <= 8 per level in FP32; the tcgen05 update uses 8
+balanced 8-bit digits and the 36 products with i + l <= 7 (8 level
+accumulators of 64 columns fill the 512 TMEM columns).  Both recombine the
+levels into one FP64 number (see the device headers that implement them).  This model uses Python
 integers for the exact parts, so it checks the scheme's claims independently
 of the GPU code: the digit bias and ranges, that every level sum is an integer
 small enough for exact FP32 accumulation, and that the result is at least as
@@ -14,8 +16,10 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
-S = 9                                   # digits
+S = 9                                   # digits of the 7-bit scheme
 BIAS = sum(64 * 128 ** k for k in range(S))
+S8 = 8                                  # digits of the 8-bit scheme
+BIAS8 = sum(128 * 256 ** k for k in range(S8))
 
 
 def fixed(x: float, E: int) -> int:
@@ -31,15 +35,23 @@ def digits(Y: int) -> list[int]:
     return [top] + rest
 
 
+def digits8(Y: int) -> list[int]:
+    Z = Y + BIAS8
+    assert 0 <= Z < 2 ** 64
+    return [((Z >> (56 - 8 * i)) & 255) - 128 for i in range(S8)]
+
+
 def exp_bound(v) -> int:
     m = float(np.max(np.abs(v)))
     return int(np.frexp(m)[1]) if m > 0 else 0
 
 
-def split_product(A: np.ndarray, B: np.ndarray, dscale: bool = True):
-    """A @ B by the scheme; returns (result, max |level sum|)."""
+def split_product(A: np.ndarray, B: np.ndarray, dscale: bool = True, eight_bit: bool = False):
+    """A @ B by the scheme (7-bit digits, 9 slices; or 8-bit digits, 8
+    slices); returns (result, max |level sum|)."""
     m, K = A.shape
     N = B.shape[1]
+    nd, base, dig = (S8, 256, digits8) if eight_bit else (S, 128, digits)
     if dscale:
         cn = np.sqrt((A * A).sum(0))
         dexp = np.where(cn > 0, np.round(np.log2(np.where(cn > 0, cn, 1))), 0).astype(int)
@@ -49,17 +61,18 @@ def split_product(A: np.ndarray, B: np.ndarray, dscale: bool = True):
     B1 = B * 2.0 ** dexp[:, None]
     Er = [exp_bound(A1[r]) for r in range(m)]
     Fk = [exp_bound(B1[:, k]) for k in range(N)]
-    ad = [[digits(fixed(A1[r, j], Er[r])) for j in range(K)] for r in range(m)]
-    bd = [[digits(fixed(B1[j, k], Fk[k])) for k in range(N)] for j in range(K)]
+    ad = [[dig(fixed(A1[r, j], Er[r])) for j in range(K)] for r in range(m)]
+    bd = [[dig(fixed(B1[j, k], Fk[k])) for k in range(N)] for j in range(K)]
     out = np.zeros((m, N))
     lmax = 0
     for r in range(m):
         for k in range(N):
-            lev = [sum(ad[r][j][i] * bd[j][k][L - i] for j in range(K) for i in range(L + 1)) for L in range(S)]
+            lev = [sum(ad[r][j][i] * bd[j][k][L - i] for j in range(K) for i in range(L + 1)) for L in range(nd)]
             lmax = max(lmax, max(abs(v) for v in lev))
-            T = sum(lev[L] * 128 ** (S - 1 - L) for L in range(S))          # exact
-            # 2^(E + F - 124) * 128^(S-1) * T, rounded once
-            out[r, k] = float(Fraction(T) * Fraction(2) ** (Er[r] + Fk[k] - 124 + 7 * (S - 1)))
+            T = sum(lev[L] * base ** (nd - 1 - L) for L in range(nd))          # exact
+            # the top digit has weight 2^56 in both schemes:
+            # 2^(E + F - 124) * 2^56 * T, rounded once
+            out[r, k] = float(Fraction(T) * Fraction(2) ** (Er[r] + Fk[k] - 124 + 56))
     return out, lmax
 
 
@@ -71,6 +84,24 @@ def test_bias_and_digit_ranges():
         assert -64 <= d[0] <= 64 and all(-64 <= di <= 63 for di in d[1:])
 
 
+def test_bias_and_digit_ranges_8bit():
+    assert BIAS8 == 0x8080808080808080
+    for Y in (0, 1, -1, 2 ** 62 - 1, -(2 ** 62 - 1), 123456789123456789, -987654321987654321):
+        d = digits8(Y)
+        assert sum(di * 256 ** (S8 - 1 - i) for i, di in enumerate(d)) == Y
+        assert -64 <= d[0] <= 64 and all(-128 <= di <= 127 for di in d[1:])
+
+
+def test_level_sums_fit_fp32_8bit_update():
+    # worst case: every digit product 128 * 128, 8 terms per level, K = 64
+    assert 8 * 64 * 128 * 128 <= 2 ** 23
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((2, 64))
+    B = np.linalg.qr(rng.standard_normal((64, 64)))[0][:, :2]
+    _, lmax = split_product(A, B, eight_bit=True)
+    assert lmax < 2 ** 23
+
+
 def test_level_sums_fit_fp32_for_256_rows():
     # worst case: every digit product 64 * 64, 9 terms per level, 256 rows
     assert 9 * 256 * 64 * 64 < 2 ** 24
@@ -80,8 +111,9 @@ def test_level_sums_fit_fp32_for_256_rows():
     assert lmax < 2 ** 24
 
 
+@pytest.mark.parametrize("eight_bit", [False, True])
 @pytest.mark.parametrize("kind", ["gaussian", "graded", "near_identity"])
-def test_columnwise_error_at_most_fp64_dot(kind):
+def test_columnwise_error_at_most_fp64_dot(kind, eight_bit):
     """Against exact rational products: the scheme's worst column error (relative
     to the column norm) is below 1 ulp and no larger than that of FP64 products
     of the same operands (which reach 2.6-4.1 ulp on these inputs)."""
@@ -95,7 +127,7 @@ def test_columnwise_error_at_most_fp64_dot(kind):
         B = (np.eye(K) + 1e-3 * rng.standard_normal((K, K)))[:, :8]
     exact = np.array([[float(sum(Fraction(A[r, j]) * Fraction(B[j, k]) for j in range(K)))
                        for k in range(B.shape[1])] for r in range(m)])
-    got, _ = split_product(A, B)
+    got, _ = split_product(A, B, eight_bit=eight_bit)
     f64 = A @ B
     eps = 2.0 ** -53
     cn = np.linalg.norm(exact, axis=0)
