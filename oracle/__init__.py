@@ -240,10 +240,13 @@ def hsvd(G, nplus: int, strategy: str = "rR", max_sweeps: int = 100):
 
 
 def block_pstep(G, V, b: int, step_pairs, inner_table, nplus: int | None = None,
-                inner_sweeps: int = 1, border: tuple[int, int] = (0, 0)):
-    """One p-step of the block-oriented method on copies of G and V."""
-    G = _fortran(G).copy(order="F")
-    V = _fortran(V).copy(order="F")
+                inner_sweeps: int = 1, border: tuple[int, int] = (0, 0), inplace: bool = False):
+    """One p-step of the block-oriented method on copies of G and V (or, with
+    inplace, on G and V themselves when they are Fortran-ordered float64)."""
+    if not (inplace and G.flags.f_contiguous and V.flags.f_contiguous and G.dtype == np.float64
+            and V.dtype == np.float64):
+        G = _fortran(G).copy(order="F")
+        V = _fortran(V).copy(order="F")
     m, n = G.shape
     nplus = n if nplus is None else nplus
     sp = np.ascontiguousarray(np.asarray(step_pairs, dtype=np.int32).reshape(-1, 2))

@@ -42,13 +42,15 @@ def test_batched_against_oracle(cuda, b):
         assert np.linalg.norm(a - (u * s) @ v.T) <= 50 * max(n, 2) * EPS * np.linalg.norm(a)
 
 
-@pytest.mark.parametrize("contraction", ["fp64", "split"])
+@pytest.mark.parametrize("contraction", ["fp64", "split_sync"])
 @pytest.mark.parametrize("b", [8, 16, 32])
 def test_batched_equals_single_path(cuda, contraction, b):
     """Same block width, ordering and contraction form: the batched solver
     performs the single path's arithmetic (extra zero rows only add exact
     zeros; the split Gram's 256-row partials start at the same rows), bit for
-    bit.  Row counts that end inside a split update block are included."""
+    bit.  Row counts that end inside a split update block are included.  The
+    batched solver's split form is the mma.sync one (both split modes), so it
+    is compared with the single path's split_sync mode."""
     mats, _, _, _ = _batch(12, seed=2 + b)
     pk = J.Packing([a.shape[0] for a in mats], [a.shape[1] for a in mats])
     U, S, V = J.svd_batched_packed(pk, pk.pack(mats, cuda), b=b, contraction=contraction)
