@@ -236,6 +236,48 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_ordering_study(args) -> None:
+    """Sweeps and time of every block ordering (Sec. 3 p-strategies, and the
+    dynamic norm-sorted ordering over rR) on the graded 8192^2 SVD and the
+    4096^2 HSVD, b = 32, split contractions; one solve each after a warm-up
+    solve, CUDA events on the solve's stream.  One JSON line per solve and a
+    summary line with the time ratios to reverse R|| (the paper's Fig. 6.1
+    reports the other static strategies 14-21 % slower than reverse R||,
+    reverse C|| about equal)."""
+    import torch
+
+    from paper_1401_2720_gb300 import build_ext
+    from paper_1401_2720_gb300 import jsvd as J
+
+    build_ext.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    orders = [("rR", False), ("rC", False), ("R", False), ("C", False), ("modulus", False), ("rR", True)]
+    summary = {}
+    for wl in args.study_workloads.split(","):
+        m, n, kind, desc = WORKLOADS[wl]
+        A = torch.from_numpy(np.ascontiguousarray(make_input(wl, args.seed).T)).to(dev).t()
+        res = {}
+        for strat, dyn in orders:
+            kw = dict(b=32, strategy=strat, dynamic_order=dyn, return_info=True, max_sweeps=args.max_sweeps)
+            solve = (lambda: J.hsvd(A, n // 2, **kw)) if kind == "hsvd" else (lambda: J.svd(A, **kw))
+            solve()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, S, _, info = solve()
+            e1.record()
+            torch.cuda.synchronize()
+            name = strat + ("+dynamic" if dyn else "")
+            res[name] = {"s": e0.elapsed_time(e1) / 1e3, "sweeps": info["sweeps"], "converged": info["converged"],
+                         "proper_rotations": info["proper_rotations"], "pairs_updated": info["pairs_updated"]}
+            print(json.dumps({"study": "orderings", "workload": desc, "ordering": name, **res[name]}), flush=True)
+        base = res["rR"]["s"]
+        summary[wl] = {k: {"time_ratio_vs_rR": v["s"] / base, "sweeps": v["sweeps"]} for k, v in res.items()}
+    print(json.dumps({"study": "orderings", "summary": summary}), flush=True)
+
+
 def run_batched(args) -> None:
     """Forward (one graph launch over all matrices) + backward (adjoint of
     L = sum w_i s_i + <C, U V^T>, cotangents formed once outside the timed
@@ -262,13 +304,14 @@ def run_batched(args) -> None:
         tuned = autotune.tune(mats)
         tune_s = time.perf_counter() - t0
         b = autotune.block_widths(pk.n, tuned)
-    U, S, V, infos, rc = J.svd_batched_packed(pk, A, b=b, return_info=True, max_sweeps=args.max_sweeps)
+    pre = dict(preprocess=True) if args.preprocess else {}
+    U, S, V, infos, rc = J.svd_batched_packed(pk, A, b=b, return_info=True, max_sweeps=args.max_sweeps, **pre)
     Us, Vs = pk.unpack_mn(U), pk.unpack_nn(V)
     dU = torch.cat([torch.from_numpy(C).to(dev).mm(v).t().reshape(-1) for C, v in zip(Cs, Vs)])
     dV = torch.cat([torch.from_numpy(C).to(dev).t().mm(u).t().reshape(-1) for C, u in zip(Cs, Us)])
     dS = torch.cat([torch.from_numpy(w).to(dev) for w in ws])
     for _ in range(args.warmup):
-        U, S, V = J.svd_batched_packed(pk, A, b=b, max_sweeps=args.max_sweeps)
+        U, S, V = J.svd_batched_packed(pk, A, b=b, max_sweeps=args.max_sweeps, **pre)
         J.svd_backward_packed(pk, U, S, V, dU, dS, dV)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -279,7 +322,8 @@ def run_batched(args) -> None:
     fwd = bwd = 0.0
     for _ in range(args.steps):
         e[0].record(stream)
-        U, S, V, infos, rc = J.svd_batched_packed(pk, A, b=b, return_info=True, max_sweeps=args.max_sweeps)
+        U, S, V, infos, rc = J.svd_batched_packed(pk, A, b=b, return_info=True, max_sweeps=args.max_sweeps,
+                                                  **pre)
         e[1].record(stream)
         dA = J.svd_backward_packed(pk, U, S, V, dU, dS, dV)
         e[2].record(stream)
@@ -320,7 +364,9 @@ def run_batched(args) -> None:
                                f"[1e-6,1] with gaps >= 1e-3, Haar U,V; forward + adjoint backward",
                    "b": (args.b if tuned is None else
                          {f"n in {autotune.BUCKETS[k]}": v for k, v in sorted(tuned.items())}),
-                   "autotune_s": None if tuned is None else tune_s},
+                   "autotune_s": None if tuned is None else tune_s,
+                   "qr_preprocessing": "matrices with m >= 2n: A P = Q [R; 0], the method on R^T"
+                   if args.preprocess else None},
         "matrices_per_s": len(pk) / (ms_step / 1e3),
         "plain_form": {"matrices": len(sample), "ms_per_matrix": plain_ms,
                        "forward_matrices_per_s": 1e3 / plain_ms,
@@ -581,6 +627,11 @@ def main():
     p.add_argument("--inner-sweeps", type=int, default=1,
                    help="inner sweeps per pivot pair: 1 = block-oriented, 30 = full block (Sec. 4.3)")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--preprocess", action="store_true",
+                   help="batched workload: QR preprocessing (column pivoting) of the matrices with m >= 2n")
+    p.add_argument("--study", default=None, choices=["orderings"],
+                   help="instead of the benchmark line: the block-ordering study")
+    p.add_argument("--study-workloads", default="graded8192,hsvd4096")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -596,7 +647,9 @@ def main():
         args.b = 16 if args.workload == "small512" else 32
     if args.strategy is None:
         args.strategy = "modulus" if args.workload == "small512" else "rR"
-    if args.impl == "reference":
+    if args.study == "orderings":
+        run_ordering_study(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched4096":
         run_batched(args)

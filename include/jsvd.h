@@ -82,6 +82,14 @@ typedef struct {
     int precision;       /* JSVD_PREC_* */
     int sort;            /* 1: sigma non-increasing (per sign block for the HSVD) */
     int contraction;     /* JSVD_CONTRACT_* (default SPLIT); used by every FP64 solver */
+    int dynamic_order;   /* 1: before every block sweep the block-columns are ordered by
+                            descending Frobenius norm and the p-strategy is applied to that
+                            order (each pair kept as (lower, higher) block index); 0: the
+                            static order (single-matrix solvers; the batched one ignores it) */
+    int preprocess;      /* jsvd_dgesvj_batched only: 1 = every matrix with m >= 2n (and n <= 1024)
+                            is first factored A P = Q [R; 0] by Householder QR with column
+                            pivoting and the method runs on the n x n R^T (Sec. 2, Eqs.
+                            (2.1)-(2.2)); U = Q [Y; 0], V = P X from R^T = X S Y^T */
 } jsvd_opts;
 
 typedef struct {
@@ -98,7 +106,8 @@ typedef struct {
 } jsvd_info;
 
 /* Fill *opts with the defaults: b = 0, strategy = JSVD_STRAT_ROW_REV,
- * inner_strategy = -1, inner_sweeps = 1, max_sweeps = 30, FP64, sort = 1. */
+ * inner_strategy = -1, inner_sweeps = 1, max_sweeps = 30, FP64, sort = 1,
+ * contraction = JSVD_CONTRACT_SPLIT, dynamic_order = 0, preprocess = 0. */
 void jsvd_default_opts(jsvd_opts *opts);
 
 /* Create a context on CUDA device `device`, issuing work on `stream`
@@ -110,6 +119,14 @@ const char *jsvd_last_error(jsvd_ctx_t ctx);
 const char *jsvd_status_string(int status);
 
 /* One-sided Jacobi SVD  A = U diag(S) V^T  (Sec. 2, Eqs. (2.3)-(2.9); Sec. 4).
+ * Column norms (the kernel Sigma) are computed by DRDSSQ (App. A).  When the
+ * largest column norm of A lies outside [2^-400, 2^400] ([2^-50, 2^50] for
+ * JSVD_PREC_MIXED), the working copy of A is first scaled by the power of two
+ * that brings it to about 1 (exact) and S is scaled back at the end, so that
+ * the Gram matrices neither overflow nor underflow; inputs whose column norms
+ * span more than about 2^500 around the largest still lose the columns below
+ * that range in the Gram matrices (their singular values then come from their
+ * own norms; the paper's remedy is a QR factorization at every level).
  *   m, n  : m >= n >= 1 (a wider matrix must be passed transposed: -2)
  *   A     : device, m x n, lda >= m; read only
  *   S     : device, n singular values (non-increasing when opts->sort)
@@ -197,6 +214,25 @@ int jsvd_dgesvj_noalloc(int m, int n, const double *A, int lda, double *S, doubl
  * with 2o <= 24 (Alg. 3.1 is run at order 2o, Alg. 3.2 expands it).
  * Host only; needs no GPU.                                                  */
 int jsvd_pivot_table(int strategy, int nblocks, int *out_pairs);
+
+/* Sums of squares of the columns of A (device, m x n, ld lda) by DRDSSQ
+ * (App. A), the parallel scaled sum the solvers use for the column norms of
+ * the kernel Sigma and for their initial scaling: ||a_j||^2 = f[j] 2^e[j]
+ * with e[j] even and 0.5 <= f[j] < 2 (0 and 0 for a zero column), without
+ * overflow or underflow for any finite input.  e, f: device arrays of n.
+ * Synchronises the context stream.                                          */
+int jsvd_column_sumsq(jsvd_ctx_t ctx, int m, int n, const double *A, int lda, int *e, double *f);
+
+/* The block p-strategy table of one sweep under the dynamic ordering
+ * (jsvd_opts.dynamic_order), computed on the GPU by the kernel the solver
+ * uses: perm (device, nblocks) receives the block-columns sorted by
+ * block_norms (device, nblocks) descending, ties by index, and pairs (device,
+ * 2*(nblocks-1)*(nblocks/2)) the static table of `strategy` with every pair
+ * (p, q) replaced by (min, max)(perm[p], perm[q]).  Synchronises the context
+ * stream.  Not in the paper (its orderings are static, Sec. 3); exposed so
+ * that the remapped table can be checked bit for bit.                       */
+int jsvd_sorted_pivot_table(jsvd_ctx_t ctx, int strategy, int nblocks, const double *block_norms, int *perm,
+                            int *pairs);
 
 /* Rotation parameters of Eqs. (4.3)-(4.6) (cs_2 form) evaluated on the GPU
  * by the same device code the sweep kernels use.  All arrays are device

@@ -76,6 +76,9 @@ def _load():
             lib.jo_colnorms.argtypes = [I, I, P, I, P]
             lib.jo_svd_adjoint.argtypes = [I, I, P, P, P, P, P, P, P]
             lib.jo_set_threads.argtypes = [I]
+            lib.jo_qrcp.argtypes = [I, I, P, I, P, P]
+            lib.jo_drdssq.argtypes = [I, P, I, P, P]
+            lib.jo_apply_q.argtypes = [I, I, P, I, P, I, P, I]
             _lib = lib
     return _lib
 
@@ -91,6 +94,7 @@ def _load_q():
             lib.jo_q_svd.argtypes = [I, I, P, I, P, I, I, I, P, P, P, P]
             lib.jo_q_loss_fd.argtypes = [I, I, P, P, D, P, P, P, I, I, I, P]
             lib.jo_q_loss_fd.restype = D
+            lib.jo_q_sumsq.argtypes = [I, P, P, P]
             _lib_q = lib
     return _lib_q
 
@@ -295,6 +299,98 @@ def block_svd(A, b: int, strategy: str = "rR", inner_strategy: str | None = None
     return dict(G=G, V=V, sweeps=int(stats[0]), converged=bool(stats[1]), rotations=int(stats[2]),
                 proper=int(stats[3]), updated=int(stats[4]), breakdowns=int(stats[5]),
                 proper_per_sweep=per[: stats[0]].copy())
+
+
+def drdssq(x) -> tuple[int, float]:
+    """App. A: ||x||^2 = f 2^e, e even, 0.5 <= f < 2, without overflow or
+    underflow; returns (e, f)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    e = ctypes.c_int(0)
+    f = ctypes.c_double(0.0)
+    _load().jo_drdssq(x.size, _ptr(x), 1, ctypes.byref(e), ctypes.byref(f))
+    return e.value, f.value
+
+
+def q_sumsq(x) -> tuple[int, float]:
+    """||x||^2 in binary128 as f 2^e, 0.5 <= f < 1 (f rounded to double)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    e = ctypes.c_int(0)
+    f = ctypes.c_double(0.0)
+    _load_q().jo_q_sumsq(x.size, _ptr(x), ctypes.byref(e), ctypes.byref(f))
+    return e.value, f.value
+
+
+def qrcp(A):
+    """A P = Q [R; 0] by Householder with column pivoting (Sec. 2, Eq. (2.1)):
+    returns (the factored array: R above, reflectors below the diagonal), tau,
+    piv (piv[j] = original column at position j)."""
+    W = _fortran(A).copy(order="F")
+    m, n = W.shape
+    tau = np.empty(n)
+    piv = np.empty(n, dtype=np.int32)
+    _load().jo_qrcp(m, n, _ptr(W), m, _ptr(tau), _ptr(piv))
+    return W, tau, piv
+
+
+def apply_q(W, tau, X):
+    """Q X for the Q of qrcp()."""
+    W = _fortran(W)
+    X = _fortran(X).copy(order="F")
+    m, n = W.shape
+    _load().jo_apply_q(m, n, _ptr(W), m, _ptr(np.ascontiguousarray(tau)), X.shape[1], _ptr(X), m)
+    return X
+
+
+def svd_qr(A, strategy: str = "modulus", max_sweeps: int = 100):
+    """The SVD with the QR preprocessing: A P = Q [R; 0], the pointwise method
+    on R^T = X S Y^T, then U = Q [Y; 0], V = P X.  Returns (U, S, V, raw)."""
+    W, tau, piv = qrcp(A)
+    m, n = W.shape
+    RT = np.asfortranarray(np.triu(W[:n, :]).T)
+    X, S, Y, r = svd(RT, strategy=strategy, max_sweeps=max_sweeps)
+    U = apply_q(W, tau, np.vstack([Y, np.zeros((m - n, n))]))
+    V = np.empty_like(X)
+    V[piv, :] = X
+    return U, S, V, r
+
+
+def block_norms(G, b: int) -> np.ndarray:
+    """Squared Frobenius norm of every block-column of width b (plain sums of
+    squares, column by column, in the oracle's column-norm routine)."""
+    s = colnorms(G)
+    return (s * s).reshape(-1, b).sum(axis=1)
+
+
+def block_svd_dynamic(A, b: int, strategy: str = "rR", nplus: int | None = None, max_sweeps: int = 30):
+    """The block-oriented method with the dynamic block ordering: before each
+    sweep the block-columns are ranked by descending norm and the static table
+    of `strategy` is applied to that ranking (pivots.norm_order, pivots.remap).
+    Returns raw G, V and statistics like block_svd."""
+    G = _fortran(A).copy(order="F")
+    m, n = G.shape
+    if n % (2 * b):
+        raise ValueError("n must be a multiple of 2b (see bordered())")
+    nb = n // b
+    V = np.asfortranarray(np.eye(n))
+    static = pivots.strategy(strategy, nb)
+    inner = strategy_array(strategy, 2 * b)
+    tot = dict(rotations=0, proper=0, updated=0, breakdowns=0)
+    per, perms = [], []
+    converged = False
+    for _ in range(max_sweeps):
+        perm = pivots.norm_order(block_norms(G, b))
+        perms.append(perm)
+        tab = pivots.to_array(pivots.remap(static, perm))
+        before = tot["proper"]
+        for step in tab:
+            G, V, st = block_pstep(G, V, b, step, inner, nplus=nplus, inplace=True)
+            for k in tot:
+                tot[k] += st[k]
+        per.append(tot["proper"] - before)
+        if per[-1] == 0:
+            converged = True
+            break
+    return dict(G=G, V=V, sweeps=len(per), converged=converged, proper_per_sweep=np.array(per), perms=perms, **tot)
 
 
 def svd_adjoint(U, S, V, dU, dS, dV) -> np.ndarray:

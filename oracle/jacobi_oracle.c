@@ -557,6 +557,158 @@ JO_API void jo_svd_adjoint(int m, int n, const real *U, const real *s,
     free(J); free(K); free(M); free(T); free(Z);
 }
 
+/* ------------------------------------------------------------------------ */
+/* DRDSSQ (App. A): the sum of squares of x (length n, finite entries) without
+ * overflow or underflow, as ||x||^2 = sigma2 * 2^e with e even and
+ * 0.5 <= sigma2 < 2 (sigma2 = 0, e = 0 for a zero vector).  Double build only.
+ * Steps, in the appendix's order:
+ *   M = max |x_i|, m = min over the non-zero |x_i|;
+ *   safe bounds mu~ = sqrt(mu / gamma), nu^ = sqrt(nu / delta_n),
+ *   delta_n = 2^ceil(lg n) delta^(1 + ceil(lg n)), gamma = 1 - eps,
+ *   delta = 1 + eps, mu / nu the smallest / largest normal numbers;
+ *   partial sums: sigma_1^2 of the x_i in [mu~, nu^] (unscaled), sigma_2^2 of
+ *   (s_2 x_i) for |x_i| > nu^ (s_2 = 2^l the largest with s_2 M <= nu^),
+ *   sigma_0^2 of (s_0 x_i) for |x_i| < mu~ (s_0 = 2^k the smallest with
+ *   s_0 m >= mu~), the exponents found by the appendix's frexp comparison;
+ *   each non-zero (s_i^-2, sigma_i^2) brought to the common form (even scale
+ *   exponent, 0.5 <= sigma^2 < 2) and the partial sums added smallest first,
+ *   the smaller rescaled to the larger's scale.                             */
+#ifndef JO_QUAD
+static int drdssq_exp(double f, double t, int upper)
+{
+    /* s = 2^j with s f <= t (upper: the largest such j) or s f >= t (the
+     * smallest such j): the appendix's frexp rule */
+    int fe, te;
+    double fy = frexp(f, &fe), ty = frexp(t, &te);
+    (void)upper;
+    return (f <= t) ? (te - fe) + (fy < ty) : (te - fe) - (fy > ty);
+}
+
+static void common_form(double sum, int scale_exp2, int *e, double *f)
+{
+    /* value = sum * 2^scale_exp2, scale_exp2 even: write as f 2^e with e even,
+     * 0.5 <= f < 2 */
+    int me;
+    double y = frexp(sum, &me);          /* sum = y 2^me, 0.5 <= y < 1 */
+    y *= 2.0;                            /* 1 <= y < 2, sum = y 2^(me-1) */
+    int m = me - 1;
+    int mp = -(((m % 2) + 2) % 2);       /* m' = -(m mod 2) in {-1, 0} */
+    *f = ldexp(y, mp);                   /* 2^m' y */
+    *e = scale_exp2 + m - mp;            /* stays even */
+}
+
+JO_API void jo_drdssq(int n, const double *x, int incx, int *e_out, double *f_out)
+{
+    const double mu = 0x1p-1022, nu = 0x1.fffffffffffffp+1023, eps = JO_EPS;
+    double M = 0.0, mn = nu;
+    for (int i = 0; i < n; ++i) {
+        double a = fabs(x[(size_t)i * incx]);
+        if (a > M) M = a;
+        if (a > 0.0 && a < mn) mn = a;
+    }
+    if (M == 0.0) { *e_out = 0; *f_out = 0.0; return; }
+    int L = 0;
+    while ((1 << L) < n) ++L;                                   /* ceil(lg n) */
+    double delta_n = ldexp(pow(1.0 + eps, 1 + L), L);
+    double mu_t = sqrt(mu / (1.0 - eps));
+    double nu_h = sqrt(nu / delta_n);
+    double s1 = 0.0, s0 = 0.0, s2 = 0.0;
+    int k0 = 0, l2 = 0;
+    if (M > nu_h) l2 = drdssq_exp(M, nu_h, 1);
+    if (mn < mu_t) k0 = drdssq_exp(mn, nextafter(mu_t, 2.0 * mu_t), 0);
+    for (int i = 0; i < n; ++i) {
+        double a = x[(size_t)i * incx];
+        double b = fabs(a);
+        if (b > nu_h) { double y = ldexp(a, l2); s2 = fma(y, y, s2); }
+        else if (b < mu_t) { double y = ldexp(a, k0); s0 = fma(y, y, s0); }
+        else s1 = fma(a, a, s1);
+    }
+    /* (s_i^-2, sigma_i^2) in common form; ||x||^2 = sigma^2 * 2^(-2 j) */
+    int ne = 0, es[3];
+    double fs[3];
+    if (s0 > 0.0) { common_form(s0, -2 * k0, &es[ne], &fs[ne]); ++ne; }
+    if (s1 > 0.0) { common_form(s1, 0, &es[ne], &fs[ne]); ++ne; }
+    if (s2 > 0.0) { common_form(s2, -2 * l2, &es[ne], &fs[ne]); ++ne; }
+    /* add smallest first: order by (e, f) lexicographically */
+    for (int a = 0; a < ne; ++a)
+        for (int b = a + 1; b < ne; ++b)
+            if (es[b] < es[a] || (es[b] == es[a] && fs[b] < fs[a])) {
+                int te = es[a]; es[a] = es[b]; es[b] = te;
+                double tf = fs[a]; fs[a] = fs[b]; fs[b] = tf;
+            }
+    int e = es[0];
+    double f = fs[0];
+    for (int a = 1; a < ne; ++a) {
+        /* smaller (e, f) rescaled to the larger's scale es[a] >= e */
+        double sum = ldexp(f, e - es[a]) + fs[a];
+        common_form(sum, es[a], &e, &f);
+    }
+    *e_out = e;
+    *f_out = f;
+}
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* QR factorization with column pivoting, A P = Q [R; 0] (the preprocessing of
+ * Sec. 2, Eqs. (2.1)-(2.2)) by Householder reflections: at step j the column
+ * of largest norm over rows j..m-1 among columns j..n-1 (ties: the lowest
+ * index) is swapped to position j, then H_j = I - tau_j v v^T (v_j = 1) with
+ * H_j x = beta e_1, beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta,
+ * v = x / (alpha - beta), is applied to columns j..n-1.  On return A holds R
+ * on and above the diagonal and the v below it; piv[j] = original column now
+ * at position j.                                                            */
+JO_API void jo_qrcp(int m, int n, real *A, int lda, real *tau, int *piv)
+{
+    real *nrm = (real *)malloc(sizeof(real) * (size_t)(n > 0 ? n : 1));
+    for (int k = 0; k < n; ++k) piv[k] = k;
+    for (int j = 0; j < n; ++j) {
+        for (int k = j; k < n; ++k)
+            nrm[k] = dot(m - j, A + j + (size_t)k * lda, A + j + (size_t)k * lda);
+        int best = j;
+        for (int k = j + 1; k < n; ++k)
+            if (nrm[k] > nrm[best]) best = k;
+        if (best != j) {
+            swap_cols(m, A + (size_t)j * lda, A + (size_t)best * lda);
+            int t = piv[j]; piv[j] = piv[best]; piv[best] = t;
+        }
+        real *x = A + j + (size_t)j * lda;
+        real alpha = x[0];
+        real sig = R_SQRT(dot(m - j, x, x));
+        if (sig == 0.0) { tau[j] = 0.0; continue; }
+        real beta = alpha >= 0.0 ? -sig : sig;
+        tau[j] = (beta - alpha) / beta;
+        real scal = 1.0 / (alpha - beta);
+        x[0] = beta;
+        for (int r = 1; r < m - j; ++r) x[r] = x[r] * scal;
+        for (int k = j + 1; k < n; ++k) {
+            real *c = A + j + (size_t)k * lda;
+            real w = c[0];
+            for (int r = 1; r < m - j; ++r) w = R_FMA(x[r], c[r], w);
+            real f = tau[j] * w;
+            c[0] = c[0] - f;
+            for (int r = 1; r < m - j; ++r) c[r] = R_FMA(-f, x[r], c[r]);
+        }
+    }
+    free(nrm);
+}
+
+/* X := Q X for the Q of jo_qrcp (reflectors in A, tau), X m x ncol.        */
+JO_API void jo_apply_q(int m, int n, const real *A, int lda, const real *tau, int ncol, real *X, int ldx)
+{
+    for (int j = n - 1; j >= 0; --j) {
+        if (tau[j] == 0.0) continue;
+        const real *v = A + j + (size_t)j * lda;
+        for (int k = 0; k < ncol; ++k) {
+            real *c = X + j + (size_t)k * ldx;
+            real w = c[0];
+            for (int r = 1; r < m - j; ++r) w = R_FMA(v[r], c[r], w);
+            real f = tau[j] * w;
+            c[0] = c[0] - f;
+            for (int r = 1; r < m - j; ++r) c[r] = R_FMA(-f, v[r], c[r]);
+        }
+    }
+}
+
 #ifdef JO_QUAD
 /* ------------------------------------------------------------------------ */
 /* binary128 entry points (double arrays in and out).                       */
@@ -600,6 +752,20 @@ static void q_svd(int m, int n, const real *A, const int *table, int nsteps, int
 }
 
 void jo_q_set_threads(int t) { jo_set_threads(t); }
+
+/* ||x||^2 in binary128 (no overflow or underflow for double inputs), as
+ * f 2^e with 0.5 <= f < 1 (f = 0 for a zero vector), f rounded to double.   */
+void jo_q_sumsq(int n, const double *x, int *e_out, double *f_out)
+{
+    real s = 0.0;
+    for (int i = 0; i < n; ++i) s += (real)x[i] * (real)x[i];
+    if (s == 0) { *e_out = 0; *f_out = 0.0; return; }
+    int e = 0;
+    while (s >= 1) { s /= 2; ++e; }
+    while (s < 0.5) { s *= 2; --e; }
+    *e_out = e;
+    *f_out = (double)s;
+}
 
 void jo_q_svd(int m, int n, const double *A, int lda, const int *table, int nsteps, int npairs,
               int max_sweeps, double *S, double *U, double *V, long long *stats)

@@ -219,3 +219,19 @@ def to_array(s: Strategy):
     import numpy as np
 
     return np.asarray(s, dtype=np.int32).reshape(len(s), len(s[0]) if s else 0, 2)
+
+
+# ---------------------------------------------------------------------------
+# Dynamic block ordering (a reading of the "column-norm-sorted" orderings;
+# the paper's strategies are static, Sec. 3): before a sweep the block-columns
+# are ranked by descending norm, ties by index, and the static table is
+# applied to that ranking; each pair is kept as (lower, higher) block index.
+def norm_order(block_norms) -> list[int]:
+    """perm[i] = the block of rank i (descending norm, stable)."""
+    idx = list(range(len(block_norms)))
+    return sorted(idx, key=lambda B: (-float(block_norms[B]), B))
+
+
+def remap(table, perm):
+    """The table with every pair (p, q) replaced by (min, max)(perm[p], perm[q])."""
+    return [[(min(perm[p], perm[q]), max(perm[p], perm[q])) for (p, q) in step] for step in table]

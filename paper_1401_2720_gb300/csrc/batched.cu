@@ -788,5 +788,7 @@ extern "C" int jsvd_dgesvj_batched(jsvd_ctx_t ctx, int batch, const int *m, cons
     if (!U || !u_off) return -10;
     if (V && !v_off) return -13;
     cudaSetDevice(ctx->device);
+    if (opts && opts->preprocess)
+        return ctx->solve_batched_qr(batch, m, n, b, A, a_off, S, s_off, U, u_off, V, v_off, opts, infos);
     return ctx->solve_batched(batch, m, n, b, A, a_off, S, s_off, U, u_off, V, v_off, opts, infos);
 }

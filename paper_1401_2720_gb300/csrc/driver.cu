@@ -54,41 +54,139 @@ __global__ void k_eye(double *__restrict__ V, int ldv, int v_rows, int n_pad) {
     }
 }
 
-// sigma_c = ||g_c||_2 (one warp per column, lane-strided sums then a fixed
-// shuffle tree); border[c] = 1 if column c has support in the border rows.
+// DRDSSQ (App. A) for one column x of length n, one warp: ||x||^2 = f 2^e
+// with e even and 0.5 <= f < 2 (f = 0, e = 0 for a zero column), no overflow
+// or underflow on the way.  M = max|x_i| and m = min of the non-zero |x_i| by
+// warp reductions; the entries inside the safe range [mu~, nu^] are summed
+// unscaled, those above (below) it scaled by 2^l (2^k) chosen by the
+// appendix's frexp rule; the partial sums are combined in the common form,
+// smallest first.
+__device__ void common_form_dev(double sum, int scale_exp2, int *e, double *f) {
+    int me;
+    double y = frexp(sum, &me) * 2.0;                 // 1 <= y < 2, sum = y 2^(me-1)
+    const int m = me - 1;
+    const int mp = -(((m % 2) + 2) % 2);
+    *f = ldexp(y, mp);
+    *e = scale_exp2 + m - mp;
+}
+__device__ int drdssq_exp_dev(double f, double t) {
+    int fe, te;
+    const double fy = frexp(f, &fe), ty = frexp(t, &te);
+    return (f <= t) ? (te - fe) + (fy < ty) : (te - fe) - (fy > ty);
+}
+__device__ void drdssq_warp(const double *__restrict__ x, int n, int *e_out, double *f_out) {
+    const int lane = threadIdx.x & 31;
+    const double mu = 0x1p-1022, nu = 0x1.fffffffffffffp+1023, eps = 0x1p-53;
+    double M = 0.0, mn = nu;
+    for (int r = lane; r < n; r += 32) {
+        const double a = fabs(x[r]);
+        M = fmax(M, a);
+        if (a > 0.0) mn = fmin(mn, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        M = fmax(M, __shfl_xor_sync(0xffffffffu, M, o));
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    if (M == 0.0) {
+        *e_out = 0;
+        *f_out = 0.0;
+        return;
+    }
+    int L = 0;
+    while ((1 << L) < n) ++L;                          // ceil(lg n)
+    double dl = 1.0;
+    for (int i = 0; i <= L; ++i) dl = __dmul_rn(dl, 1.0 + eps);
+    const double delta_n = ldexp(dl, L);
+    const double mu_t = sqrt(mu / (1.0 - eps)), nu_h = sqrt(nu / delta_n);
+    const int l2 = M > nu_h ? drdssq_exp_dev(M, nu_h) : 0;
+    const int k0 = mn < mu_t ? drdssq_exp_dev(mn, nextafter(mu_t, 2.0 * mu_t)) : 0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int r = lane; r < n; r += 32) {
+        const double a = x[r], b = fabs(a);
+        if (b > nu_h) { const double y = ldexp(a, l2); s2 = __fma_rn(y, y, s2); }
+        else if (b < mu_t) { const double y = ldexp(a, k0); s0 = __fma_rn(y, y, s0); }
+        else s1 = __fma_rn(a, a, s1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 = __dadd_rn(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+        s1 = __dadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+        s2 = __dadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+    }
+    int ne = 0, es[3];
+    double fs[3];
+    if (s0 > 0.0) { common_form_dev(s0, -2 * k0, &es[ne], &fs[ne]); ++ne; }
+    if (s1 > 0.0) { common_form_dev(s1, 0, &es[ne], &fs[ne]); ++ne; }
+    if (s2 > 0.0) { common_form_dev(s2, -2 * l2, &es[ne], &fs[ne]); ++ne; }
+    for (int a = 0; a < ne; ++a)
+        for (int b = a + 1; b < ne; ++b)
+            if (es[b] < es[a] || (es[b] == es[a] && fs[b] < fs[a])) {
+                const int te = es[a]; es[a] = es[b]; es[b] = te;
+                const double tf = fs[a]; fs[a] = fs[b]; fs[b] = tf;
+            }
+    int e = es[0];
+    double f = fs[0];
+    for (int a = 1; a < ne; ++a) common_form_dev(ldexp(f, e - es[a]) + fs[a], es[a], &e, &f);
+    *e_out = e;
+    *f_out = f;
+}
+
+// e[c], f[c] = DRDSSQ of column c (rows [0, rows)); *emax (if not null) =
+// max over the non-zero columns of e + 8192.
+__global__ void k_col_drdssq(const double *__restrict__ G, int ldg, int rows, int ncols, int *__restrict__ e,
+                             double *__restrict__ f, unsigned long long *__restrict__ emax) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (w >= ncols) return;
+    int ee;
+    double ff;
+    drdssq_warp(G + (size_t)w * ldg, rows, &ee, &ff);
+    if ((threadIdx.x & 31) == 0) {
+        if (e) e[w] = ee;
+        if (f) f[w] = ff;
+        if (emax && ff > 0.0) atomicMax(emax, (unsigned long long)(ee + 8192));
+    }
+}
+
+// X *= 2^k (exact for the entries this is applied to: the scale is chosen so
+// that no entry over- or underflows beyond what the input already did).
+__global__ void k_scale_pow2(double *__restrict__ X, size_t count, int k) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        X[e] = ldexp(X[e], k);
+}
+
+// sigma_c = ||g_c||_2 by DRDSSQ (one warp per column); border[c] = 1 if
+// column c has support in the border rows.
 __global__ void k_colnorms(const double *__restrict__ G, int ldg, int rows, int m, int k,
                            int n_pad, double *__restrict__ sigma, int *__restrict__ border) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (warp >= n_pad) return;
     const double *g = G + (size_t)warp * ldg;
-    double s = 0.0;
     int bd = 0;
-    for (int r = lane; r < rows; r += 32) {
-        const double x = g[r];
-        s = __fma_rn(x, x, s);
-        if (r >= m && r < m + k && x != 0.0) bd = 1;
-    }
-    for (int off = 16; off > 0; off >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off));
+    for (int r = m + lane; r < m + k && r < rows; r += 32)
+        if (g[r] != 0.0) bd = 1;
     bd = __any_sync(0xffffffffu, bd);
+    int e;
+    double f;
+    drdssq_warp(g, rows, &e, &f);            // App. A: ||g||^2 = f 2^e, e even
     if (lane == 0) {
-        sigma[warp] = __dsqrt_rn(s);
+        sigma[warp] = ldexp(__dsqrt_rn(f), e / 2);
         border[warp] = bd;
     }
 }
 
 // Output column i takes workspace column perm[i]:
-//   U(:, i) = g / sigma (zero column if sigma = 0), S(i) = sigma,
+//   U(:, i) = g / sigma (zero column if sigma = 0), S(i) = sigma 2^-unscale
+//   (undoing the solver's initial power-of-two scaling of G),
 //   V(r, i) = js(r) * W(row(r), perm[i]) * js(i)   (V = J W J for the HSVD).
 __global__ void k_finalize(const double *__restrict__ G, int ldg, const double *__restrict__ W,
                            int ldw, const double *__restrict__ sigma, const int *__restrict__ perm,
-                           int m, int n, int ins, int k, int nplus, int hyperbolic,
+                           int m, int n, int ins, int k, int nplus, int hyperbolic, int unscale,
                            double *__restrict__ S, double *__restrict__ U, int ldu,
                            double *__restrict__ Vo, int ldv) {
     const int i = blockIdx.y;
     const int c = perm[i];
     const double sg = sigma[c];
-    if (blockIdx.x == 0 && threadIdx.x == 0) S[i] = sg;
+    if (blockIdx.x == 0 && threadIdx.x == 0) S[i] = ldexp(sg, -unscale);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
         const double g = G[(size_t)c * ldg + r];
         U[(size_t)i * ldu + r] = sg > 0.0 ? __ddiv_rn(g, sg) : 0.0;
@@ -139,6 +237,51 @@ __global__ void k_sigma_perm(const double *__restrict__ sigma, const int *__rest
     if (border[c]) atomicOr(err, 2ull);
     // the J = -1 block starts after the nplus_w - k real columns of the J = +1 block
     perm[(pos ? 0 : nplus_w - k) + rank] = c;
+}
+
+// Dynamic block ordering (one reading of "column-norm-sorted orderings"):
+// bnorm[B] = sum of the squared norms of the b columns of block-column B
+// (rows [0, rows)), one warp per block-column.
+__global__ void k_block_norms(const void *__restrict__ Gv, int fp32, int ldg, int rows, int b, int nb,
+                              double *__restrict__ bnorm) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+    if (w >= nb) return;
+    double s = 0.0;
+    for (int c = 0; c < b; ++c) {
+        const size_t col = (size_t)(w * b + c) * ldg;
+        for (int r = lane; r < rows; r += 32) {
+            const double x = fp32 ? (double)reinterpret_cast<const float *>(Gv)[col + r]
+                                  : reinterpret_cast<const double *>(Gv)[col + r];
+            s = __fma_rn(x, x, s);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off));
+    if (lane == 0) bnorm[w] = s;
+}
+
+// perm[i] = the block-column of rank i when ordered by bnorm descending, ties
+// by block index (a stable sort: the rank of block B is the number of blocks
+// that precede it); then the sweep's table: pair (p, q) of the static table
+// becomes (min, max)(perm[p], perm[q]).
+__global__ void k_block_order(const double *__restrict__ bnorm, int nb, const int *__restrict__ stab, int npairs_total,
+                              int *__restrict__ perm, int *__restrict__ dtab) {
+    extern __shared__ int s_perm[];
+    for (int B = threadIdx.x; B < nb; B += blockDim.x) {
+        const double v = bnorm[B];
+        int rank = 0;
+        for (int o = 0; o < nb; ++o) {
+            const double u = bnorm[o];
+            rank += (u > v || (u == v && o < B)) ? 1 : 0;
+        }
+        s_perm[rank] = B;
+    }
+    __syncthreads();
+    for (int B = threadIdx.x; B < nb; B += blockDim.x) perm[B] = s_perm[B];
+    for (int e = threadIdx.x; e < npairs_total; e += blockDim.x) {
+        const int p = s_perm[stab[2 * e]], q = s_perm[stab[2 * e + 1]];
+        dtab[2 * e] = min(p, q);
+        dtab[2 * e + 1] = max(p, q);
+    }
 }
 
 __global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, size_t count) {
@@ -274,6 +417,7 @@ jsvd_ctx::~jsvd_ctx() {
 
 void jsvd_ctx::release_memory() {
     for (Buffer *b : {&g, &v, &part, &vprime, &vflag, &counters, &sigma, &border, &perm, &bslice, &bexp, &dexp, &gexp,
+                      &dyn_tab, &dyn_norm, &q_meta, &q_w, &q_tau, &q_piv, &q_in, &q_u, &q_s, &q_v,
                       &g32, &v32,
                       &tmp_a, &tmp_b, &tmp_g, &b_mats, &b_units, &b_g, &b_v, &b_part, &b_vp, &b_vflag,
                       &b_tab, &b_cnt, &b_stat, &b_starts, &b_sigma, &b_border, &b_perm, &b_misc, &b_bsl,
@@ -486,6 +630,11 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         k_eye<<<1024, 256, 0, stream>>>(V, v_rows, v_rows, n_pad);
         prof_launches[4] += 1;
     }
+    // column norms by DRDSSQ (App. A): the largest norm decides the initial
+    // scaling below
+    k_col_drdssq<<<(n_pad * 32 + 255) / 256, 256, 0, stream>>>(G, g_rows, g_rows, n_pad, nullptr, nullptr,
+                                                               cnt + kCntNormExp);
+    prof_launches[4] += 1;
     if (profiling && (rc = ensure_events(6 * (size_t)(nb - 1)))) return rc;
     if ((rc = check("init"))) return rc;
     cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize, cudaMemcpyDeviceToHost, stream);
@@ -494,11 +643,44 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         last_error = "input holds Inf or NaN";
         return JSVD_ERR_NONFINITE;
     }
+    // Initial rescaling (App. A: "the input factor should be initially
+    // rescaled"): if the largest column norm 2^(e/2) lies outside [2^-lim,
+    // 2^lim] (lim = 400 for the FP64 sweeps; 50 when the first sweeps run in
+    // FP32), G is multiplied by 2^-(e/2), exactly, so that the Gram matrices
+    // (squares of column norms) neither overflow nor underflow; S is scaled
+    // back at the end, U and V do not change.
+    int prescale = 0;
+    if (host_counters[kCntNormExp] != 0) {
+        const int half = ((int)host_counters[kCntNormExp] - 8192) / 2;
+        const int lim = (o.precision == JSVD_PREC_MIXED) ? 50 : 400;
+        if (half > lim || half < -lim) {
+            prescale = -half;
+            k_scale_pow2<<<1024, 256, 0, stream>>>(G, (size_t)g_rows * n_pad, prescale);
+            prof_launches[4] += 1;
+        }
+    }
 
     PStepArgs a{};
     a.ldg = g_rows; a.g_rows = g_rows;
     a.ldv = v_rows; a.v_rows = v_rows;
     a.table = dtab; a.npairs = npairs; a.inner = dinner;
+    const bool dynamic = o.dynamic_order != 0;
+    const int tab_pairs = (nb - 1) * npairs;
+    if (dynamic) {
+        if ((rc = ensure(dyn_tab, sizeof(int) * 2 * (size_t)tab_pairs + sizeof(int) * nb))) return rc;
+        if ((rc = ensure(dyn_norm, sizeof(double) * (size_t)nb))) return rc;
+    }
+    // order the block-columns by descending norm for the coming sweep (the
+    // static table is applied to that order)
+    auto reorder = [&]() {
+        int *dt = (int *)dyn_tab.ptr;
+        k_block_norms<<<(nb * 32 + 255) / 256, 256, 0, stream>>>(a.G, a.fp32, a.ldg, a.g_rows, b, nb,
+                                                                 (double *)dyn_norm.ptr);
+        k_block_order<<<1, 1024, sizeof(int) * nb, stream>>>((const double *)dyn_norm.ptr, nb, dtab, tab_pairs,
+                                                             dt + 2 * tab_pairs, dt);
+        prof_launches[4] += 2;
+        a.table = dt;
+    };
     a.b = b; a.nplus = nplus_w; a.inner_sweeps = o.inner_sweeps;
     a.bord_lo = ins; a.bord_hi = ins + k;
     a.part = (double *)part.ptr; a.g_chunks = g_chunks;
@@ -523,6 +705,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         *conv = 0;
         unsigned long long first_proper = 0;
         while (*done < limit) {
+            if (dynamic) reorder();
             cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
             const bool side = side_streams && a.V != nullptr && !a.split;
             const int nslot = side ? ring : 1;
@@ -658,7 +841,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
                                                           (int *)perm.ptr, cnt + kCntErr);
     dim3 grid((std::max(m, n) + 255) / 256 < 8 ? (std::max(m, n) + 255) / 256 : 8, n);
     k_finalize<<<grid, 256, 0, stream>>>(G, g_rows, V, v_rows, dsig, (int *)perm.ptr, m, n, ins, k,
-                                         nplus, hyperbolic ? 1 : 0, S, U, ldu, Vout, ldv);
+                                         nplus, hyperbolic ? 1 : 0, prescale, S, U, ldu, Vout, ldv);
     prof_launches[4] += 3;  // column norms, ordering, output assembly
     if ((rc = check("finalize"))) return rc;
     cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize, cudaMemcpyDeviceToHost, stream);
@@ -686,6 +869,8 @@ void jsvd_default_opts(jsvd_opts *o) {
     o->precision = JSVD_PREC_FP64;
     o->sort = 1;
     o->contraction = JSVD_CONTRACT_SPLIT;
+    o->dynamic_order = 0;
+    o->preprocess = 0;
 }
 
 int jsvd_create(jsvd_ctx_t *ctx, int device, void *stream) {
@@ -787,6 +972,41 @@ int jsvd_dhsvj(jsvd_ctx_t ctx, int m, int n, int n_plus, const double *G, int ld
     if (V && ldv < n) return -11;
     cudaSetDevice(ctx->device);
     return ctx->solve(m, n, n_plus, G, ldg, S, U, ldu, V, ldv, opts, info, n_plus < n);
+}
+
+int jsvd_column_sumsq(jsvd_ctx_t ctx, int m, int n, const double *A, int lda, int *e, double *f) {
+    if (!ctx) return -1;
+    if (m < 1) return -2;
+    if (n < 1) return -3;
+    if (!A) return -4;
+    if (lda < m) return -5;
+    if (!e) return -6;
+    if (!f) return -7;
+    cudaSetDevice(ctx->device);
+    k_col_drdssq<<<(n * 32 + 255) / 256, 256, 0, ctx->stream>>>(A, lda, m, n, e, f, nullptr);
+    if (int rc = ctx->check("column sums of squares")) return rc;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ctx->check("column sums of squares sync") ? JSVD_ERR_CUDA
+                                                                                                         : JSVD_ERR_CUDA;
+    return 0;
+}
+
+int jsvd_sorted_pivot_table(jsvd_ctx_t ctx, int strategy, int nblocks, const double *block_norms, int *perm,
+                            int *pairs) {
+    if (!ctx) return -1;
+    if (strategy < 0 || strategy > 4) return -2;
+    if (nblocks < 2 || nblocks % 2 || nblocks > 8192) return -3;
+    if (!block_norms) return -4;
+    if (!perm) return -5;
+    if (!pairs) return -6;
+    cudaSetDevice(ctx->device);
+    const int *stab = nullptr;
+    if (int rc = ctx->table(strategy, nblocks, &stab)) return rc;
+    const int total = (nblocks - 1) * (nblocks / 2);
+    k_block_order<<<1, 1024, sizeof(int) * nblocks, ctx->stream>>>(block_norms, nblocks, stab, total, perm, pairs);
+    if (int rc = ctx->check("sorted pivot table")) return rc;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ctx->check("sorted pivot table sync") ? JSVD_ERR_CUDA
+                                                                                                        : JSVD_ERR_CUDA;
+    return 0;
 }
 
 int jsvd_rotation_params(jsvd_ctx_t ctx, int count, const double *hpp, const double *hqq,

@@ -25,11 +25,14 @@ struct jsvd_ctx {
 
     // workspace (grown on demand, freed with the context)
     Buffer g, v, part, vprime, vflag, counters, sigma, border, perm;
-    Buffer bslice, bexp, dexp, gexp;       // split right factors, column exponent bounds (tensor-core contractions)
+    Buffer bslice, bexp, dexp, gexp;
+    Buffer dyn_tab, dyn_norm;              // dynamic block ordering: sweep table + permutation, block norms       // split right factors, column exponent bounds (tensor-core contractions)
     Buffer g32, v32, tmp_a, tmp_b, tmp_g;  // mixed precision
     Buffer b_mats, b_units, b_g, b_v, b_part, b_vp, b_vflag, b_tab, b_cnt, b_stat, b_starts, b_sigma,
         b_border, b_perm, b_misc, b_bsl, b_bex, b_dex, b_gexp;   // batched solver
     Buffer adj_w, adj_meta, adj_desc;      // adjoint
+    Buffer q_meta, q_w, q_tau, q_piv, q_in, q_u, q_s, q_v;   // batched QR preprocessing
+    std::vector<unsigned char> q_meta_host;
     unsigned long long *host_counters = nullptr;  // pinned
     std::map<std::pair<int, int>, Buffer> tables;  // (strategy, order) -> device table
     std::map<std::pair<int, int>, std::vector<int>> host_tables;
@@ -67,6 +70,10 @@ struct jsvd_ctx {
                       const long long *a_off, double *S, const long long *s_off, double *U,
                       const long long *u_off, double *V, const long long *v_off, const jsvd_opts *opts,
                       jsvd_info *infos);
+    int solve_batched_qr(int batch, const int *m, const int *n, const int *b, const double *A,
+                         const long long *a_off, double *S, const long long *s_off, double *U,
+                         const long long *u_off, double *V, const long long *v_off, const jsvd_opts *opts,
+                         jsvd_info *infos);
     int backward(int batch, const int *m, const int *n, const double *U, const long long *u_off,
                  const double *S, const long long *s_off, const double *V, const long long *v_off,
                  const double *dU, const double *dS, const double *dV, double *dA, const long long *a_off);

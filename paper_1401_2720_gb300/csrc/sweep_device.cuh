@@ -28,6 +28,7 @@ enum {
     kCntOff = 4,       // max normalized off-diagonal |h_ij|/sqrt(h_ii h_jj), double bits
     kCntErr = 5,       // device-side error flags
     kCntInner = 6,     // inner sweeps performed, summed over the pivot pairs
+    kCntNormExp = 7,   // at set-up: max over the columns of the DRDSSQ exponent + 8192
     kCntSize = 8
 };
 

@@ -39,7 +39,8 @@ class JsvdError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("strategy", ctypes.c_int), ("inner_strategy", ctypes.c_int),
                 ("inner_sweeps", ctypes.c_int), ("max_sweeps", ctypes.c_int),
-                ("precision", ctypes.c_int), ("sort", ctypes.c_int), ("contraction", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("sort", ctypes.c_int), ("contraction", ctypes.c_int),
+                ("dynamic_order", ctypes.c_int), ("preprocess", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -60,7 +61,7 @@ EXPORTED = ["jsvd_default_opts", "jsvd_create", "jsvd_destroy", "jsvd_set_stream
             "jsvd_last_error", "jsvd_status_string", "jsvd_dgesvj", "jsvd_dhsvj",
             "jsvd_pivot_table", "jsvd_rotation_params", "jsvd_profile", "jsvd_profile_read",
             "jsvd_fp64_peak", "jsvd_bf16_mma_peak", "jsvd_dgesvj_batched", "jsvd_dgesvj_backward",
-            "jsvd_dgesvj_noalloc"]
+            "jsvd_dgesvj_noalloc", "jsvd_sorted_pivot_table", "jsvd_column_sumsq"]
 
 
 def library():
@@ -94,6 +95,8 @@ def library():
             lib.jsvd_dgesvj_backward.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.jsvd_dgesvj_noalloc.argtypes = [I, I, P, I, P, P, I, P, I, ctypes.POINTER(Opts),
                                                 ctypes.POINTER(Info), P]
+            lib.jsvd_sorted_pivot_table.argtypes = [P, I, I, P, P, P]
+            lib.jsvd_column_sumsq.argtypes = [P, I, I, P, I, P, P]
             _lib = lib
     return _lib
 
@@ -121,7 +124,8 @@ def _raise(rc: int, h) -> None:
 
 def make_opts(b: int = 0, strategy: str = "rR", inner_strategy: str | None = None,
               inner_sweeps: int = 1, max_sweeps: int = 30, precision: str = "fp64",
-              sort: bool = True, contraction: str = "split") -> Opts:
+              sort: bool = True, contraction: str = "split", dynamic_order: bool = False,
+              preprocess: bool = False) -> Opts:
     o = Opts()
     library().jsvd_default_opts(ctypes.byref(o))
     o.b = b
@@ -132,6 +136,8 @@ def make_opts(b: int = 0, strategy: str = "rR", inner_strategy: str | None = Non
     o.precision = PRECISIONS[precision]
     o.sort = 1 if sort else 0
     o.contraction = CONTRACTIONS[contraction]
+    o.dynamic_order = 1 if dynamic_order else 0
+    o.preprocess = 1 if preprocess else 0
     return o
 
 
@@ -198,6 +204,36 @@ def pivot_table(strategy: str, nblocks: int) -> np.ndarray:
     if rc:
         raise JsvdError(rc, f"no {strategy} table of order {nblocks}")
     return out.reshape(nblocks - 1, nblocks // 2, 2)
+
+
+def column_sumsq(A: torch.Tensor):
+    """DRDSSQ (App. A) of every column of A: (e, f) with ||a_j||^2 = f_j 2^e_j."""
+    buf, ld = _colmajor(A)
+    m, n = A.shape
+    e = torch.empty(n, dtype=torch.int32, device=A.device)
+    f = torch.empty(n, dtype=torch.float64, device=A.device)
+    h = context(A.device.index)
+    rc = library().jsvd_column_sumsq(h, m, n, buf.data_ptr(), ld, e.data_ptr(), f.data_ptr())
+    if rc:
+        _raise(rc, h)
+    return e, f
+
+
+def sorted_pivot_table(strategy: str, block_norms: torch.Tensor):
+    """The dynamic ordering's sweep table computed by the library's kernel:
+    (perm, pairs) with perm the block-columns by descending norm (ties by
+    index) and pairs (nblocks-1, nblocks/2, 2) the remapped static table."""
+    dev = block_norms.device
+    nb = block_norms.numel()
+    norms = block_norms.to(torch.float64).contiguous()
+    perm = torch.empty(nb, dtype=torch.int32, device=dev)
+    pairs = torch.empty((nb - 1) * nb, dtype=torch.int32, device=dev)
+    h = context(dev.index)
+    rc = library().jsvd_sorted_pivot_table(h, STRATEGIES[strategy], nb, norms.data_ptr(), perm.data_ptr(),
+                                           pairs.data_ptr())
+    if rc:
+        _raise(rc, h)
+    return perm, pairs.reshape(nb - 1, nb // 2, 2)
 
 
 def rotation_params(hpp: torch.Tensor, hqq: torch.Tensor, hpq: torch.Tensor, hyperbolic: torch.Tensor):

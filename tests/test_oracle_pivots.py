@@ -67,3 +67,54 @@ def test_invariant_detects_broken_tables():
     bad = [list(x) for x in s]
     bad[1][0], bad[2][0] = bad[2][0], bad[1][0]        # duplicate / collision
     assert not P.is_pstrategy(bad, 8)
+
+
+# ---------------------------------------------------------------------------
+# dynamic block ordering: a remapped parallel strategy is still a parallel
+# strategy (Def. 3.1: every p-step a set of disjoint pairs, every pair once
+# per sweep), and the ranking is a stable descending sort
+@pytest.mark.parametrize("name", ["modulus", "rR", "C"])
+@pytest.mark.parametrize("nb", [4, 10, 16, 48])
+def test_remapped_table_is_a_parallel_strategy(name, nb):
+    import random
+
+    rnd = random.Random(nb)
+    perm = list(range(nb))
+    rnd.shuffle(perm)
+    tab = P.remap(P.strategy(name, nb), perm)
+    seen = set()
+    for step in tab:
+        cols = [c for pq in step for c in pq]
+        assert sorted(cols) == list(range(nb))
+        for p, q in step:
+            assert p < q and (p, q) not in seen
+            seen.add((p, q))
+    assert len(seen) == nb * (nb - 1) // 2
+    # the identity ranking gives the static table back
+    assert P.remap(P.strategy(name, nb), list(range(nb))) == P.strategy(name, nb)
+
+
+def test_norm_order_is_a_stable_descending_sort():
+    norms = [3.0, 1.0, 3.0, 7.0, 1.0, 0.0]
+    assert P.norm_order(norms) == [3, 0, 2, 1, 4, 5]
+
+
+@pytest.mark.parametrize("b", [4, 8])
+def test_block_method_with_dynamic_order(b):
+    """The dynamic ordering changes only which block pairs meet when: the
+    method converges to the same singular values (LAPACK, normwise) and
+    G = A V keeps holding; the first ranking is that of the input's blocks."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1401_2720_gb300 import inputs as I
+
+    A = I.graded_columns(120, 8 * b, 3.0, seed=b)[:, ::-1].copy(order="F")   # ascending column norms
+    r = O.block_svd_dynamic(A, b, strategy="rR")
+    assert r["converged"]
+    assert r["perms"][0] == P.norm_order(O.block_norms(A, b))
+    assert r["perms"][0][0] == 8 - 1        # the largest block comes first
+    s = np.sort(O.colnorms(r["G"]))[::-1]
+    sl = np.linalg.svd(A, compute_uv=False)
+    assert np.max(np.abs(s - sl)) <= 100 * np.sqrt(8 * b) * 2.0 ** -53 * sl[0]
+    assert np.linalg.norm(A @ r["V"] - r["G"]) <= 1e-13 * np.linalg.norm(A)

@@ -198,3 +198,27 @@ def test_block_method_duplicate_column_exact_breakdown(b):
     _, sp, _, _ = O.svd(A)
     assert sp[-1] <= 50 * n * EPS * sp[0]
     assert np.max(np.abs(sp - sl)) <= 100 * np.sqrt(n) * EPS * sl[0]
+
+
+@pytest.mark.parametrize("mn", [(200, 40), (96, 48), (501, 17)])
+def test_qr_preprocessing(mn):
+    """Sec. 2, Eqs. (2.1)-(2.2): A P = Q [R; 0] with Q orthogonal, R upper
+    triangular with non-increasing diagonal magnitudes (column pivoting), and
+    the SVD through R^T equals LAPACK's; on a graded tall matrix the method on
+    R^T needs fewer sweeps than on A."""
+    m, n = mn
+    A = I.graded_columns(m, n, 4.0, seed=m)[:, np.random.default_rng(n).permutation(n)].copy(order="F")
+    W, tau, piv = O.qrcp(A)
+    R = np.triu(W[:n, :])
+    Q = O.apply_q(W, tau, np.eye(m))
+    assert _orth(Q) <= 20 * m * EPS
+    assert np.linalg.norm(Q[:, :n] @ R - A[:, piv]) <= 20 * m * EPS * np.linalg.norm(A)
+    d = np.abs(np.diag(R))
+    assert np.all(d[:-1] >= d[1:] * (1 - 1e-12))
+    U, S, V, r = O.svd_qr(A)
+    sl = np.linalg.svd(A, compute_uv=False)
+    assert np.max(np.abs(S - sl)) <= 100 * np.sqrt(n) * EPS * sl[0]
+    assert _orth(U) <= 50 * n * EPS and _orth(V) <= 50 * n * EPS
+    assert np.linalg.norm(A - (U * S) @ V.T) <= 50 * n * EPS * np.linalg.norm(A)
+    _, _, _, r0 = O.svd(A, strategy="modulus")
+    assert r["sweeps"] < r0["sweeps"]
