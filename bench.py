@@ -302,9 +302,12 @@ def run_batched(args) -> None:
 
         t0 = time.perf_counter()
         tuned = autotune.tune(mats)
-        tune_s = time.perf_counter() - t0
         b = autotune.block_widths(pk.n, tuned)
+        strat, strat_times = autotune.tune_strategy(mats, tuned)
+        tune_s = time.perf_counter() - t0
     pre = dict(preprocess=True) if args.preprocess else {}
+    if tuned is not None:
+        pre["strategy"] = strat
     U, S, V, infos, rc = J.svd_batched_packed(pk, A, b=b, return_info=True, max_sweeps=args.max_sweeps, **pre)
     Us, Vs = pk.unpack_mn(U), pk.unpack_nn(V)
     dU = torch.cat([torch.from_numpy(C).to(dev).mm(v).t().reshape(-1) for C, v in zip(Cs, Vs)])
@@ -365,6 +368,7 @@ def run_batched(args) -> None:
                    "b": (args.b if tuned is None else
                          {f"n in {autotune.BUCKETS[k]}": v for k, v in sorted(tuned.items())}),
                    "autotune_s": None if tuned is None else tune_s,
+                   "strategy": None if tuned is None else {"chosen": strat, "sample_s": strat_times},
                    "qr_preprocessing": "matrices with m >= 2n: A P = Q [R; 0], the method on R^T"
                    if args.preprocess else None},
         "matrices_per_s": len(pk) / (ms_step / 1e3),

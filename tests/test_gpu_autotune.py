@@ -23,3 +23,18 @@ def test_autotune_table_and_tuned_solve(cuda):
     for a, s in zip(mats, pk.unpack_n(S)):
         sl = np.linalg.svd(a, compute_uv=False)
         assert np.max(np.abs(_np(s) - sl)) <= 1e-12 * sl[0]
+
+
+def test_autotune_strategy(cuda):
+    mats, _, _, _ = I.workload_batch(40, seed=23, m_hi=160)
+    table = autotune.tune(mats, sample=10, repeats=1)
+    best, times = autotune.tune_strategy(mats, table, sample=20, repeats=1)
+    assert best in ("rR", "rC", "modulus") and set(times) == {"rR", "rC", "modulus"}
+    assert times[best] == min(times.values())
+    pk = J.Packing([a.shape[0] for a in mats], [a.shape[1] for a in mats])
+    U, S, V, infos, rc = J.svd_batched_packed(pk, pk.pack(mats, cuda), b=autotune.block_widths(pk.n, table),
+                                              strategy=best, return_info=True)
+    assert rc == 0
+    for a, s in zip(mats, pk.unpack_n(S)):
+        sl = np.linalg.svd(a, compute_uv=False)
+        assert np.max(np.abs(_np(s) - sl)) <= 1e-12 * sl[0]
