@@ -79,4 +79,43 @@ __device__ __forceinline__ void rot_apply(double &x, double &y, bool hyperbolic,
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same rotation in FP32 (the first stage of the mixed FP32 -> FP64 solver,
+// whose sweeps only precondition the FP64 ones): Eqs. (4.3)-(4.6) with
+// eps = 2^-24, so sqrt(eps) = 2^-12 and sqrt(2 / eps) = 2^12.5 (rounded to
+// FP32), every operation a correctly rounded FP32 intrinsic.
+constexpr float kSqrtEps32 = 0x1p-12f;
+constexpr float kSqrt2OverEps32 = 5792.6187f;
+
+struct RotF {
+    float cs;
+    float tn;
+};
+
+__device__ __forceinline__ RotF rot_params_f(float hpp, float hqq, float hpq, bool hyperbolic) {
+    const float t = hyperbolic ? -1.0f : 1.0f;
+    const float h = hyperbolic ? __fadd_rn(hqq, hpp) : __fsub_rn(hqq, hpp);
+    float ct2 = __fdiv_rn(h, __fmul_rn(2.0f, hpq));
+    if (hyperbolic) ct2 = -ct2;
+    if (hyperbolic && !(fabsf(ct2) > 1.0f)) ct2 = copysignf(1.25f, ct2);
+    const float a2 = fabsf(ct2);
+    float act;
+    if (a2 >= kSqrt2OverEps32)
+        act = __fmul_rn(2.0f, a2);
+    else if (!hyperbolic && a2 < kSqrtEps32)
+        act = __fadd_rn(a2, 1.0f);
+    else
+        act = __fadd_rn(a2, __fsqrt_rn(__fmaf_rn(ct2, ct2, t)));
+    RotF r;
+    r.tn = copysignf(__frcp_rn(act), ct2);
+    r.cs = act >= kSqrt2OverEps32 ? 1.0f : __fdiv_rn(act, __fsqrt_rn(__fmaf_rn(act, act, t)));
+    return r;
+}
+
+__device__ __forceinline__ bool needs_rotation_f(float hpp, float hqq, float hpq, float c_eps) {
+    const float a = fabsf(hpq);
+    if (a == 0.0f) return false;
+    return !(a < __fmul_rn(c_eps, __fmul_rn(__fsqrt_rn(hpp), __fsqrt_rn(hqq))));
+}
+
 }  // namespace jsvd

@@ -101,16 +101,26 @@ __device__ __forceinline__ void store_digits8(unsigned char *dst, int slice_stri
 #undef JSVD_S8
 }
 
+// Level L of a length-64 contraction as an int.  The top digits d_0 lie in
+// [-64, 64] (|Y| < 2^62) and the others in [-128, 127], so |lev_L| <= 2^22 for
+// L <= 4 (for L = 4: 64 (2 * 64 * 128 + 3 * 128^2) = 2^22) and one FP32 add of
+// 1.5 * 2^23 puts the integer into the low significand bits; levels 5..7 can
+// reach 64 (2 * 64 * 128 + (L - 1) * 128^2) <= 1.75 * 2^22, beyond that
+// trick's range, and take the exact conversion instruction.
+__device__ __forceinline__ int level_int(float v, int L) {
+    return L <= 4 ? __float_as_int(__fadd_rn(v, 12582912.0f)) - 0x4B400000 : __float2int_rn(v);
+}
+
 // The FP64 value 2^(e - 68) * T, T = sum_L lev[L] 256^(7-L), rounded once to
 // nearest (ties to even), in 64-bit integer arithmetic.  Level values are
-// exact integers, |lev| <= 2^23, so T = hi 2^32 + lo with |hi|, |lo| < 2^48;
+// exact integers, |lev| < 2^23, so T = hi 2^32 + lo with |hi|, |lo| < 2^48;
 // |T| is brought to the form M 2^32 + R (0 <= R < 2^32, M < 2^48), whose
 // leading 64 bits are rounded to 53.
 __device__ __forceinline__ double combine(const float (&lv)[kSlices], int e) {
     long long v[kSlices];
 #pragma unroll
     for (int L = 0; L < kSlices; ++L)
-        v[L] = (long long)(__float_as_int(__fadd_rn(lv[L], 12582912.0f)) - 0x4B400000);
+        v[L] = (long long)level_int(lv[L], L);
     const long long hi = v[0] * 16777216ll + v[1] * 65536ll + v[2] * 256ll + v[3];
     const long long lo = v[4] * 16777216ll + v[5] * 65536ll + v[6] * 256ll + v[7];
     // T = H 2^32 + L, 0 <= L < 2^32 (floor division of lo by 2^32)
@@ -172,10 +182,11 @@ __device__ __forceinline__ double combine(const float (&lv)[kSlices], int e) {
 //   T = D0 2^56 + F,  F = d1 d2 ... d7 (bytes, 0 <= F < 2^56),
 // |T| is shifted left by whole words and then bits until its leading one is
 // at bit 95 of a 96-bit value, and rounded once to 53 bits, ties to even.
-__device__ __forceinline__ double combine32(const float (&lv)[kSlices], int e) {
-    int l[kSlices];
-#pragma unroll
-    for (int L = 0; L < kSlices; ++L) l[L] = __float_as_int(__fadd_rn(lv[L], 12582912.0f)) - 0x4B400000;
+//
+// combine_levels takes the level values as ints (any |lev| < 2^30, e.g. the
+// Gram's sums of several accumulators); combine32 converts a length-64
+// contraction's FP32 levels first.
+__device__ __forceinline__ double combine_levels(const int (&l)[kSlices], int e) {
     uint32_t d[kSlices];
     int c = 0;
 #pragma unroll
@@ -184,7 +195,7 @@ __device__ __forceinline__ double combine32(const float (&lv)[kSlices], int e) {
         d[L] = (uint32_t)x & 255u;
         c = x >> 8;                      // arithmetic: floor division by 256
     }
-    const int D0 = l[0] + c;             // |D0| < 2^24
+    const int D0 = l[0] + c;             // |D0| < 2^31 for |lev| < 2^30
     // F = (Fh << 32) | Fl, Fh = d1 d2 d3 (24 bits), Fl = d4 d5 d6 d7
     const uint32_t Fl0 = __byte_perm(__byte_perm(d[7], d[6], 0x0040u), __byte_perm(d[5], d[4], 0x0040u), 0x5410u);
     const uint32_t Fh0 = __byte_perm(__byte_perm(d[3], d[2], 0x0040u), d[1], 0x5410u);
@@ -222,6 +233,13 @@ __device__ __forceinline__ double combine32(const float (&lv)[kSlices], int e) {
     if (be >= 1 && be <= 2046) return __hiloint2double((int)(sign | ((uint32_t)be << 20) | mh), (int)ml);
     const double r = __hiloint2double((int)(sign | (1075u << 20) | mh), (int)ml);   // +-mant, exact
     return split::scale_slow(r, ex - 52 + e - 68);
+}
+
+__device__ __forceinline__ double combine32(const float (&lv)[kSlices], int e) {
+    int l[kSlices];
+#pragma unroll
+    for (int L = 0; L < kSlices; ++L) l[L] = level_int(lv[L], L);
+    return combine_levels(l, e);
 }
 
 // Right-factor images of one pivot pair (see above): version 0 = D V' for

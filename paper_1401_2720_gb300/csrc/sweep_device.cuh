@@ -226,8 +226,8 @@ __device__ __forceinline__ void nbar_arrive() {
 }
 
 // Element arithmetic of the inner sweep in the type RT of R and V': FP64, or
-// FP32 in the first stage of the mixed solver.  The rotation parameters are
-// always computed in FP64 (Eqs. (4.3)-(4.6)) and rounded to RT to be applied.
+// FP32 in the first stage of the mixed solver, whose rotations (Eqs.
+// (4.3)-(4.6), relative test with eps = 2^-24) are then FP32 as well.
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double add_t(double a, double b) { return __dadd_rn(a, b); }
@@ -285,21 +285,39 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsig
                 tqq = add_t(tqq, __shfl_xor_sync(0xffffffffu, tqq, off));
                 tpq = add_t(tpq, __shfl_xor_sync(0xffffffffu, tpq, off));
             }
-            const double hpp = (double)tpp, hqq = (double)tqq, hpq = (double)tpq;
             const int gp = block_col(P, Q, b, p), gq = block_col(P, Q, b, q);
             const bool hyp = gp < nplus && gq >= nplus;
             const bool border = (gp >= bord_lo && gp < bord_hi) || (gq >= bord_lo && gq < bord_hi);
-            const bool rho = !border && needs_rotation(hpp, hqq, hpq, c_eps);
+            bool rho, swap = false, proper;
+            RT cs_t, tn_t;
             Rot rot{1.0, 0.0};
-            if (rho) rot = rot_params(hpp, hqq, hpq, hyp);
-            bool swap = false;
-            if (!hyp && !border) {
-                const double npp = rho ? __fma_rn(-rot.tn, hpq, hpp) : hpp;
-                const double nqq = rho ? __fma_rn(rot.tn, hpq, hqq) : hqq;
-                swap = (gq < nplus && npp < nqq) || (gp >= nplus && npp > nqq);
+            if constexpr (sizeof(RT) == sizeof(double)) {
+                const double hpp = tpp, hqq = tqq, hpq = tpq;
+                rho = !border && needs_rotation(hpp, hqq, hpq, c_eps);
+                if (rho) rot = rot_params(hpp, hqq, hpq, hyp);
+                if (!hyp && !border) {
+                    const double npp = rho ? __fma_rn(-rot.tn, hpq, hpp) : hpp;
+                    const double nqq = rho ? __fma_rn(rot.tn, hpq, hqq) : hqq;
+                    swap = (gq < nplus && npp < nqq) || (gp >= nplus && npp > nqq);
+                }
+                cs_t = (RT)rot.cs;
+                tn_t = (RT)rot.tn;
+                proper = is_proper(rot);
+            } else {
+                // FP32 sweeps: the rotation itself in FP32 (rotation.cuh)
+                RotF rf{1.0f, 0.0f};
+                rho = !border && needs_rotation_f(tpp, tqq, tpq, (float)c_eps);
+                if (rho) rf = rot_params_f(tpp, tqq, tpq, hyp);
+                if (!hyp && !border) {
+                    const float npp = rho ? __fmaf_rn(-rf.tn, tpq, tpp) : tpp;
+                    const float nqq = rho ? __fmaf_rn(rf.tn, tpq, tqq) : tqq;
+                    swap = (gq < nplus && npp < nqq) || (gp >= nplus && npp > nqq);
+                }
+                cs_t = rf.cs;
+                tn_t = rf.tn;
+                proper = rf.cs != 1.0f;
+                rot = Rot{(double)rf.cs, (double)rf.tn};
             }
-            const RT cs_t = (RT)rot.cs, tn_t = (RT)rot.tn;
-            const bool proper = is_proper(rot);
             if (st >= 2) {
                 if (slot) nbar_sync<jb::kEmpty0 + 1, NT>(); else nbar_sync<jb::kEmpty0, NT>();
             }

@@ -20,8 +20,9 @@ __global__ void __launch_bounds__(Cfg<BB>::kGramThreads) gram_partial(PStepArgs 
 
 // NT = kJacThreads: any number of inner sweeps; NT = 2 kJacThreads: one inner
 // sweep with V' rotated by a second thread group (jacobi_sweep_pipelined),
-// R and V' held in RT (float in the FP32 sweeps of the mixed solver; the
-// rotation parameters, Cholesky and counters stay FP64).
+// R and V' held in RT (float in the FP32 sweeps of the mixed solver, whose
+// rotations are then FP32 too; the sum of the Gram partials and the Cholesky
+// stay FP64).
 template <int BB, int NT, typename RT = double>
 __global__ void __launch_bounds__(NT) pair_jacobi(PStepArgs a) {
     extern __shared__ __align__(16) double smem[];

@@ -74,6 +74,8 @@ void launch_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
 void launch_split_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
 // The tcgen05 block update (update_tc.cu): G and V of every pair with V' != I.
 void launch_update_tc(int BB, const PStepArgs &a, cudaStream_t s);
+// The Gram partials on tcgen05 (gram_tc.cu), when PStepArgs::tc is set.
+void launch_gram_tc(int BB, const PStepArgs &a, cudaStream_t s);
 // gexp[j] = exponent bound of column j of G (rows [0, rows)), one CTA per column.
 void launch_col_maxexp(const double *G, int ldg, int rows, int ncols, int *gexp, cudaStream_t s);
 

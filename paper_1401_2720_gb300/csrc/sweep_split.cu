@@ -93,6 +93,10 @@ static void launch_split_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
     using S = SplitCfg<BB>;
     configure_split_once<BB>();
     if (ph == Phase::Gram) {
+        if (a.tc) {
+            launch_gram_tc(BB, a, s);
+            return;
+        }
         const int ctas = (a.g_chunks + S::kChunksPerCta - 1) / S::kChunksPerCta;
         gram_split<BB><<<dim3(ctas, a.npairs), S::kGThreads, gram_split_smem<BB>(), s>>>(a);
         return;

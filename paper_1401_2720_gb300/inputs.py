@@ -146,3 +146,20 @@ def duplicated_pm1_column(A, j0: int, j1: int, count: int = 16, seed=0) -> np.nd
     B[rows, j0] = rng.choice([-1.0, 1.0], count)
     B[:, j1] = B[:, j0]
     return np.asfortranarray(B)
+
+
+def coherent_digit_columns(m: int, n: int, seed=0) -> np.ndarray:
+    """A_kj = s_k y_j + M_kj / 16 with signs s_k = +-1, integers M_kj in
+    [-3, 3] and y_j = t_j 2^-62, t_j = 0x207F7F7F7F7F7C00 + 2^50 j (exact
+    doubles in [0.5, 0.6)).  Every entry's fixed-point value trunc(x 2^62)
+    shares the bytes 0x7F of t_j below the top one, with the row's sign, so
+    products of the 8-bit digits add up coherently over the rows: level sums of
+    a 256-row contraction reach ~2^24, the largest the digit form must carry
+    exactly.  The random integer part (top digit only) keeps the matrix well
+    conditioned."""
+    rng = rng_of(seed)
+    t = np.array([0x207F7F7F7F7F7C00 + (j << 50) for j in range(n)], dtype=np.float64)
+    y = np.ldexp(t, -62)
+    s = rng.choice([-1.0, 1.0], m)
+    M = rng.integers(-3, 4, size=(m, n)).astype(np.float64)
+    return np.asfortranarray(s[:, None] * y[None, :] + M / 16.0)

@@ -134,3 +134,32 @@ def test_split_agrees_with_fp64_form(cuda):
     assert np.max(np.abs(S1 - S0)) <= 1e-12 * S0[0]
     assert np.max(np.abs(S1 - S0) / S0) <= 1e-10
     assert _orth(_np(V1)) <= 50 * 768 * EPS
+
+
+@pytest.mark.parametrize("b", [8, 16, 32])
+def test_split_coherent_digits(cuda, b):
+    """Columns whose 8-bit digits below the top one are the same in every row
+    (up to the row's sign): the digit products add up coherently, so the
+    Gram's level sums over a 256-row chunk come close to 2^24, the largest the
+    FP32 accumulators hold exactly, and the update's level sums pass 2^22.
+    The columns are nearly parallel (a dominant rank-one part), so the first
+    sweep's rotation angles are sensitive to the Gram's rounding: after one
+    block sweep the split form must be as close to the oracle, column by
+    column, as the FP64 FMA form is (within a factor 4, or 1e-12); the
+    converged singular values must match LAPACK."""
+    m, n = 768, 4 * b
+    A = I.coherent_digit_columns(m, n, seed=b)
+    r = O.block_svd(A, b, strategy="rR", max_sweeps=1)
+    cn = np.linalg.norm(r["G"], axis=0)
+    errs = {}
+    for form in ("split", "fp64"):
+        U, S, V, info = J.svd(_t(A, cuda), b=b, strategy="rR", max_sweeps=1, sort=False, return_info=True,
+                              contraction=form)
+        G = _np(U) * _np(S)[None, :]
+        errs[form] = np.max(np.abs(G - r["G"]), axis=0) / cn
+    assert np.all(errs["split"] <= np.maximum(1e-12, 4.0 * errs["fp64"])), (errs["split"].max(), errs["fp64"].max())
+    U, S, V, info = J.svd(_t(A, cuda), b=b, return_info=True, contraction="split")
+    sl = np.linalg.svd(A, compute_uv=False)
+    assert info["converged"] and info["breakdowns"] == 0
+    assert np.max(np.abs(_np(S) - sl)) <= 1e-13 * sl[0]
+    assert _orth(_np(V)) <= 50 * n * EPS

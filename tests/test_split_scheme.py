@@ -135,3 +135,54 @@ def test_columnwise_error_at_most_fp64_dot(kind, eight_bit):
     err_f64 = (np.linalg.norm(f64 - exact, axis=0) / cn).max() / eps
     assert err_split <= 1.0
     assert err_split <= err_f64
+
+
+def _stacked_gram_levels(Dg: np.ndarray, BB: int):
+    """The tcgen05 Gram's accumulators for one 256-row chunk, modelled with
+    integers: Dg[i, k, c] = digit i of row k, column c.  The A operand stacks
+    SF = 128 / BB slices (slice g SF + s in rows s BB .. s BB + BB - 1), the
+    B operand holds slices 0 .. 7 - g SF, and MMA g adds its products at
+    column block g SF, so lane s BB + c, block j accumulates
+    sum_{g SF <= j} sum_k d_{g SF + s}(k, c) d_{j - g SF}(k, n).  Returns the
+    per-column sums [lane, block, n] and the levels assembled from them."""
+    SF = 128 // BB
+    acc = np.zeros((128, 8, BB), dtype=object)
+    for g in range(8 // SF):
+        for s in range(SF):
+            for j in range(g * SF, 8):
+                for c in range(BB):
+                    acc[s * BB + c, j, :] += [int(Dg[g * SF + s, :, c] @ Dg[j - g * SF, :, n]) for n in range(BB)]
+    lev = np.zeros((BB, BB, 8), dtype=object)
+    for L in range(8):
+        for s in range(SF):
+            if L - s >= 0:
+                lev[:, :, L] += acc[s * BB:(s + 1) * BB, L - s, :]
+    return acc, lev
+
+
+@pytest.mark.parametrize("BB", [16, 64])
+@pytest.mark.parametrize("kind", ["coherent", "extreme"])
+def test_stacked_gram_column_sums_exact_and_levels(BB, kind):
+    """Every tensor-memory column of the stacked tcgen05 Gram sums at most
+    8 / SF digit products over 256 rows, so it stays within 2^24 (exact in
+    FP32) even for inputs whose digits add coherently (the assembled level
+    sums then pass 2^24), and the assembled levels are the level sums
+    sum_{i+l=L} sum_k d_i d_l."""
+    from paper_1401_2720_gb300 import inputs as I
+    if kind == "coherent":
+        A = I.coherent_digit_columns(256, BB, seed=BB)
+        Dg = np.array([[digits8(fixed(A[k, c], 0)) for k in range(256)] for c in range(BB)]).transpose(2, 1, 0)
+    else:
+        # the most negative digits (Y = -63 2^56 - sum_{i>0} 128 256^(7-i) > -2^62) in
+        # every row and column: all products positive, the largest level sums
+        Dg = np.full((8, 256, BB), -128)
+        Dg[0] = -63
+    Dg = Dg.astype(np.int64)
+    acc, lev = _stacked_gram_levels(Dg, BB)
+    assert max(abs(int(v)) for v in acc.flat) <= 2 ** 24
+    for c in range(0, BB, 7):
+        for n in range(0, BB, 5):
+            for L in range(8):
+                assert lev[c, n, L] == sum(int(Dg[i, :, c] @ Dg[L - i, :, n]) for i in range(L + 1))
+    if kind == "extreme":
+        assert max(abs(int(v)) for v in lev.flat) > 2 ** 24
