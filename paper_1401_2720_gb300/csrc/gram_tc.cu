@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
         GWaiter wait{s_abort};
         // the 8 entries of this thread in round rd of unit u
         auto src_of = [&](long long u, int rd) {
-            const int pair = (int)(u / a.g_chunks), chunk = (int)(u % a.g_chunks);
+            const int uu = (int)u, pair = uu / a.g_chunks, chunk = uu - pair * a.g_chunks;
             const int P = a.table[2 * (a.step * a.npairs + pair)];
             const int Q = a.table[2 * (a.step * a.npairs + pair) + 1];
             return G + (size_t)gcol(P, Q, a.b, c) * a.ldg + (size_t)chunk * kGramRowsSplit +

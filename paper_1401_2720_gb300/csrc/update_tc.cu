@@ -263,12 +263,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_tc(PStepArgs a) {
                 if ((col % 16 == 0 || g == 0) && use >= 1) wait(&B.a_empty[slot], (uint32_t)((use - 1) & 1));
             }
             asm volatile("bar.sync %0, %1;" ::"n"(kBarProd), "n"(32 * kProdWarps) : "memory");
-            // first pass: the row's exponent bound over this thread's entries,
-            // 16 loads in flight at a time (the rest prefetched into L2)
-            int m = split::kNoExp;
+            // the next tile's entries of this thread into L2, so that neither
+            // of its passes waits on HBM
+            if (t + 1 < t1) {
+                const double *cur = src;
+                const size_t ldc = ldx;
+                locate_src(t + 1);
 #pragma unroll
-            for (int c = 16; c < U::kCPT; ++c)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(src + c * ldx));
+                for (int c = 0; c < U::kCPT; ++c) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + c * ldx));
+                src = cur;
+                ldx = ldc;
+            }
+            // first pass: the row's exponent bound over this thread's entries,
+            // 16 loads in flight at a time
+            int m = split::kNoExp;
+            if (j == 0) {
+#pragma unroll
+                for (int c = 16; c < U::kCPT; ++c)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(src + c * ldx));
+            }
 #pragma unroll 1
             for (int c1 = 0; c1 < U::kCPT; c1 += 16) {
                 constexpr int NG = U::kCPT < 16 ? U::kCPT : 16;
