@@ -46,15 +46,16 @@ UPDATE_BYTES_PER_PAIR_ROW = 477.94e6 / (64 * 8192)
 # launch): ncu, 4096x4096 graded, b = 32, every pair updated, 279.16 MB read +
 # 209.30 MB written for 2 x 64 pairs x 4096 rows.
 SPLIT_UPDATE_BYTES_PER_PAIR_ROW = 488.461e6 / (2 * 64 * 4096)
-# bf16 digit products per FP64 product in the split contractions: the Gram and
-# the mma.sync update use 9 7-bit slices (levels i + l <= 8: 45 products), the
-# tcgen05 update 8 8-bit slices (levels i + l <= 7: 36 products)
+# bf16 digit products per FP64 product in the split contractions: the mma.sync
+# Gram and update (contraction "split_sync") use 9 7-bit slices (levels
+# i + l <= 8: 45 products), the tcgen05 Gram and update (the default "split")
+# 8 8-bit slices (levels i + l <= 7: 36 products)
 SPLIT_PRODUCTS = 45
-TC_UPDATE_PRODUCTS = 36
+TC_PRODUCTS = 36
 # dram__bytes_read.sum + dram__bytes_write.sum of one update_tc<64> launch (ncu,
-# 4096x4096 graded, b = 32, first sweep: every pair updated) divided by its
-# (pair, row) units; None until measured for the current kernel
-TC_UPDATE_BYTES_PER_PAIR_ROW = None
+# 4096x4096 graded, b = 32, first sweep: every pair updated; 283.18 MB read +
+# 208.69 MB written) divided by its 64 pairs x 8192 (G and V) rows
+TC_UPDATE_BYTES_PER_PAIR_ROW = 491.868e6 / (64 * 8192)
 
 WORKLOADS = {
     # name: (m, n, generator, description)
@@ -548,13 +549,13 @@ def run_gpu(args) -> None:
                 f"{peak_dfma:.3f} TFLOP/s")
     if args.contraction in ("split", "split_sync") and dom in ("gram", "update"):
         # tensor-core kernels: each FP64 product is `products` bf16 digit products
-        products = TC_UPDATE_PRODUCTS if (args.contraction == "split" and dom == "update") else SPLIT_PRODUCTS
+        products = TC_PRODUCTS if args.contraction == "split" else SPLIT_PRODUCTS
         bf16_peak, bf16_src = bf16_peak_tflops(sustained=True)
         tensor = products * achieved
         roofline = {"bound": "tensor", "achieved": tensor, "peak": bf16_peak, "unit": "TFLOP/s",
                     "frac": tensor / bf16_peak, "traffic": traffic,
-                    "kernel": {"gram": "gram_split",
-                               "update": "update_tc" if args.contraction == "split" else "update_split"}[dom],
+                    "kernel": ({"gram": "gram_tc", "update": "update_tc"} if args.contraction == "split"
+                               else {"gram": "gram_split", "update": "update_split"})[dom],
                     "launches": d_launch,
                     "peak_source": bf16_src + " (of measured); achieved = "
                                    f"{products} bf16 digit products x the kernel's algorithmic FP64 flops / "
@@ -574,9 +575,11 @@ def run_gpu(args) -> None:
     if args.contraction in ("split", "split_sync"):
         kernels["update"]["note"] = ("update of G and V in one launch (tcgen05, 8-bit digits)" if args.contraction ==
                                      "split" else "update of G and V in one launch (mma.sync, 7-bit digits)")
+        kernels["gram"]["note"] = ("Gram partials on tcgen05 (8-bit digits)" if args.contraction == "split"
+                                   else "Gram partials on mma.sync (7-bit digits)")
         for c in ("gram", "update"):
             if kernels[c]["tflops"]:
-                pr = TC_UPDATE_PRODUCTS if (args.contraction == "split" and c == "update") else SPLIT_PRODUCTS
+                pr = TC_PRODUCTS if args.contraction == "split" else SPLIT_PRODUCTS
                 kernels[c]["tensor_tflops"] = pr * kernels[c]["tflops"]
         kernels["update_v"]["note"] = "no side-stream V update with split contractions"
     else:
