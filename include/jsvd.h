@@ -244,6 +244,16 @@ int jsvd_rotation_params(jsvd_ctx_t ctx, int count, const double *hpp,
                          const int *hyperbolic, double *cs, double *tn,
                          int *proper);
 
+/* The relative orthogonality test of Sec. 4.3 as the sweep kernels evaluate
+ * it: rho[i] = 1 unless hpq[i] == 0 or |hpq[i]| < c_eps * (sqrt(hpp[i]) *
+ * sqrt(hqq[i])) with every operation correctly rounded.  The kernels decide
+ * most cases from the squares and fall back to the square roots inside a
+ * guard band; exposed so that the decisions can be compared bit for bit with
+ * a CPU evaluation.  All arrays are device memory of length count; the call
+ * synchronises the context stream.                                          */
+int jsvd_relative_test(jsvd_ctx_t ctx, int count, const double *hpp, const double *hqq,
+                       const double *hpq, double c_eps, int *rho);
+
 /* ---- instrumentation ---------------------------------------------------
  * Kernel classes: 0 = Gram partials, 1 = per-pair Cholesky + inner sweep,
  * 2 = block update (Eq. (2.9)) on the solve's main stream (G, or G and V when

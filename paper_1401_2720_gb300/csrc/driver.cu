@@ -329,6 +329,13 @@ __global__ void k_rot_params(int count, const double *hpp, const double *hqq, co
     proper[i] = r.cs != 1.0;
 }
 
+__global__ void k_rel_test(int count, const double *hpp, const double *hqq, const double *hpq, double c_eps,
+                           int *rho) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    rho[i] = needs_rotation(hpp[i], hqq[i], hpq[i], c_eps, __dmul_rn(c_eps, c_eps)) ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // context
 
@@ -1019,6 +1026,18 @@ int jsvd_rotation_params(jsvd_ctx_t ctx, int count, const double *hpp, const dou
     k_rot_params<<<(count + 255) / 256, 256, 0, ctx->stream>>>(count, hpp, hqq, hpq, hyperbolic, cs, tn, proper);
     if (int rc = ctx->check("rotation params")) return rc;
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ctx->check("rotation sync") ? JSVD_ERR_CUDA : JSVD_ERR_CUDA;
+    return 0;
+}
+
+int jsvd_relative_test(jsvd_ctx_t ctx, int count, const double *hpp, const double *hqq, const double *hpq,
+                       double c_eps, int *rho) {
+    if (!ctx) return -1;
+    if (count < 0) return -2;
+    if (count == 0) return 0;
+    cudaSetDevice(ctx->device);
+    k_rel_test<<<(count + 255) / 256, 256, 0, ctx->stream>>>(count, hpp, hqq, hpq, c_eps, rho);
+    if (int rc = ctx->check("relative test")) return rc;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return JSVD_ERR_CUDA;
     return 0;
 }
 

@@ -53,11 +53,37 @@ __device__ __forceinline__ Rot rot_params(double hpp, double hqq, double hpq, bo
 }
 
 // Relative orthogonality test of Sec. 4.3 (subphase 2): no rotation when
-// h_pq = 0 or |h_pq| < c(eps) * (sqrt(h_pp) * sqrt(h_qq)), c(eps) = eps*sqrt(nhat).
-__device__ __forceinline__ bool needs_rotation(double hpp, double hqq, double hpq, double c_eps) {
+// h_pq = 0 or |h_pq| < c(eps) * (sqrt(h_pp) * sqrt(h_qq)), c(eps) = eps*sqrt(nhat),
+// every operation correctly rounded.
+__device__ __forceinline__ bool needs_rotation_exact(double hpp, double hqq, double hpq, double c_eps) {
     const double a = fabs(hpq);
     if (__double_as_longlong(a) == 0) return false;
     return !nonneg_lt(a, __dmul_rn(c_eps, __dmul_rn(__dsqrt_rn(hpp), __dsqrt_rn(hqq))));
+}
+
+// The same decision, mostly without the two square roots (each about eight
+// FP64-pipe instructions, the scarce unit): with T the correctly rounded
+// threshold above, T = c sqrt(h_pp h_qq) (1 + t), |t| <= 4u (u = 2^-53), and
+// the squares compared in FP64, RN(a^2) = a^2 (1 + d1), RN(c^2 RN(h_pp h_qq))
+// = c^2 h_pp h_qq (1 + d2), |d1| <= u, |d2| <= 3u (c^2 given correctly
+// rounded), so a squared ratio outside [1 - m, 1 + m], m = 2^-48, decides
+// a >= T or a < T for certain (m / 2 - 3u > 4u).  Inside that band, or when
+// an exponent lies outside [-400, 400] (products could leave the normal
+// range), the exact evaluation decides.  Bit-identical decisions.
+__device__ __forceinline__ bool needs_rotation(double hpp, double hqq, double hpq, double c_eps, double c_eps2) {
+    const double a = fabs(hpq);
+    if (__double_as_longlong(a) == 0) return false;
+    const int ea = (int)((__double_as_longlong(a) >> 52) & 0x7ff) - 1023;
+    const int ep = (int)((__double_as_longlong(hpp) >> 52) & 0x7ff) - 1023;
+    const int eq = (int)((__double_as_longlong(hqq) >> 52) & 0x7ff) - 1023;
+    if (hpp > 0.0 && hqq > 0.0 && ea >= -400 && ea <= 400 && ep >= -400 && ep <= 400 && eq >= -400 &&
+        eq <= 400) {
+        const double lhs = __dmul_rn(a, a);
+        const double rhs = __dmul_rn(c_eps2, __dmul_rn(hpp, hqq));
+        if (lhs > __dmul_rn(rhs, 1.0 + 0x1p-48)) return true;
+        if (lhs < __dmul_rn(rhs, 1.0 - 0x1p-48)) return false;
+    }
+    return needs_rotation_exact(hpp, hqq, hpq, c_eps);
 }
 
 // cs != 1 (cs > 0)

@@ -253,6 +253,7 @@ __device__ __forceinline__ void rot_apply_t(RT &x, RT &y, bool hyperbolic, RT cs
 template <int BB, typename RT = double>
 __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsigned char *tab, int P, int Q,
                                                        int b, int nplus, int bord_lo, int bord_hi, double c_eps,
+                                                       double c_eps2,
                                                        int &my_rot, int &my_proper, int &changed) {
     using C = Cfg<BB>;
     constexpr int NH = C::kJacThreads;        // threads per side
@@ -293,7 +294,7 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsig
             Rot rot{1.0, 0.0};
             if constexpr (sizeof(RT) == sizeof(double)) {
                 const double hpp = tpp, hqq = tqq, hpq = tpq;
-                rho = !border && needs_rotation(hpp, hqq, hpq, c_eps);
+                rho = !border && needs_rotation(hpp, hqq, hpq, c_eps, c_eps2);
                 if (rho) rot = rot_params(hpp, hqq, hpq, hyp);
                 if (!hyp && !border) {
                     const double npp = rho ? __fma_rn(-rot.tn, hpq, hpp) : hpp;
@@ -511,11 +512,12 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
 
     // (5) inner sweeps of the pointwise one-sided method on R (Sec. 4.3)
     const double c_eps = eps * sqrt((double)BB);   // c(eps) = eps sqrt(nhat), nhat = BB
+    const double c_eps2 = __dmul_rn(c_eps, c_eps);
     int my_rot = 0, my_proper = 0, changed = 0, sweeps_done = 0;
     if constexpr (NT == 2 * C::kJacThreads) {
         // one inner sweep, V' rotated one step behind R by the second half of
         // the threads
-        jacobi_sweep_pipelined<BB, RT>(Vt, Rt, tab, P, Q, b, nplus, bord_lo, bord_hi, c_eps, my_rot, my_proper,
+        jacobi_sweep_pipelined<BB, RT>(Vt, Rt, tab, P, Q, b, nplus, bord_lo, bord_hi, c_eps, c_eps2, my_rot, my_proper,
                                        changed);
         sweeps_done = 1;
     } else {
@@ -548,7 +550,7 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
             const int gp = block_col(P, Q, b, p), gq = block_col(P, Q, b, q);
             const bool hyp = gp < nplus && gq >= nplus;
             const bool border = (gp >= bord_lo && gp < bord_hi) || (gq >= bord_lo && gq < bord_hi);
-            const bool rho = !border && needs_rotation(hpp, hqq, hpq, c_eps);
+            const bool rho = !border && needs_rotation(hpp, hqq, hpq, c_eps, c_eps2);
             Rot rot{1.0, 0.0};
             if (rho) rot = rot_params(hpp, hqq, hpq, hyp);
             bool swap = false;

@@ -61,7 +61,7 @@ EXPORTED = ["jsvd_default_opts", "jsvd_create", "jsvd_destroy", "jsvd_set_stream
             "jsvd_last_error", "jsvd_status_string", "jsvd_dgesvj", "jsvd_dhsvj",
             "jsvd_pivot_table", "jsvd_rotation_params", "jsvd_profile", "jsvd_profile_read",
             "jsvd_fp64_peak", "jsvd_bf16_mma_peak", "jsvd_dgesvj_batched", "jsvd_dgesvj_backward",
-            "jsvd_dgesvj_noalloc", "jsvd_sorted_pivot_table", "jsvd_column_sumsq"]
+            "jsvd_dgesvj_noalloc", "jsvd_sorted_pivot_table", "jsvd_column_sumsq", "jsvd_relative_test"]
 
 
 def library():
@@ -86,6 +86,7 @@ def library():
             lib.jsvd_dhsvj.argtypes = [P, I, I, I, P, I, P, P, I, P, I, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
             lib.jsvd_pivot_table.argtypes = [I, I, P]
             lib.jsvd_rotation_params.argtypes = [P, I, P, P, P, P, P, P, P]
+            lib.jsvd_relative_test.argtypes = [P, I, P, P, P, D, P]
             lib.jsvd_profile.argtypes = [P, I]
             lib.jsvd_profile_read.argtypes = [P, P, P, P, I]
             lib.jsvd_fp64_peak.argtypes = [P, D, P, P]
@@ -251,6 +252,20 @@ def rotation_params(hpp: torch.Tensor, hqq: torch.Tensor, hpq: torch.Tensor, hyp
     if rc:
         _raise(rc, h)
     return cs, tn, pr.bool()
+
+
+def relative_test(hpp: torch.Tensor, hqq: torch.Tensor, hpq: torch.Tensor, c_eps: float) -> torch.Tensor:
+    """The sweep kernels' relative orthogonality test (Sec. 4.3), as bools."""
+    n = hpp.numel()
+    dev = hpp.device
+    rho = torch.empty(n, dtype=torch.int32, device=dev)
+    args = [t.to(dtype=torch.float64).contiguous() for t in (hpp, hqq, hpq)]
+    h = context(dev.index)
+    rc = library().jsvd_relative_test(h, n, args[0].data_ptr(), args[1].data_ptr(), args[2].data_ptr(),
+                                      float(c_eps), rho.data_ptr())
+    if rc:
+        _raise(rc, h)
+    return rho.bool()
 
 
 KERNEL_CLASSES = ("gram", "jacobi", "update", "update_v", "other")
