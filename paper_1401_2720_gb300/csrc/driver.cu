@@ -690,7 +690,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
     };
     a.b = b; a.nplus = nplus_w; a.inner_sweeps = o.inner_sweeps;
     a.bord_lo = ins; a.bord_hi = ins + k;
-    a.part = (double *)part.ptr; a.g_chunks = g_chunks;
+    a.part = (double *)part.ptr; a.g_chunks = g_chunks; a.g_parts = g_chunks;
     a.vprime = (double *)vprime.ptr; a.vflag = (int *)vflag.ptr;
     a.counters = cnt;
 
@@ -831,6 +831,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
     if (split) {
         // Gram partials of 256 rows; column exponent bounds of the current G
         a.g_chunks = g_rows / kGramRowsSplit;
+        a.g_parts = tc ? gram_tc_parts(a) : a.g_chunks;
         a.gexp = (int *)gexp.ptr;
         launch_col_maxexp(G, g_rows, g_rows, n_pad, a.gexp, stream);
         prof_launches[4] += 1;

@@ -32,6 +32,7 @@
 //   warp 24     allocates TMEM; its lane 0 issues the MMAs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "split8.cuh"
@@ -68,7 +69,9 @@ template <int BB> struct GramCfg {
     static constexpr int kXBuf = 8 * kXCols * 128 * 4; // one drain buffer: 32 KB
     static constexpr int kOffX = kStageBytesTotal;
     static constexpr int kOffE = kOffX + 2 * kXBuf;    // int [BB]: the unit's column exponents (epilogue)
-    static constexpr int kOffBar = kOffE + BB * 4;     // a_full[kSlots], a_empty[kSlots], d_full, d_empty, done
+    static constexpr int kPk = BB * (BB + 1) / 2;      // outputs (packed lower triangle)
+    static constexpr int kOffAcc = kOffE + BB * 4;     // double [kPk]: the run's sum over its chunks
+    static constexpr int kOffBar = kOffAcc + kPk * 8;  // a_full[kSlots], a_empty[kSlots], d_full, d_empty, done
     static constexpr int kNumBars = 2 * kSlots + 3;
     static constexpr int kOffMisc = kOffBar + 8 * kNumBars;           // tmem base, abort flag
     static constexpr int kSmem = kOffMisc + 16;
@@ -119,6 +122,7 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     int *xbuf = reinterpret_cast<int *>(sm + C::kOffX);
     int *ecx = reinterpret_cast<int *>(sm + C::kOffE);
+    double *accp = reinterpret_cast<double *>(sm + C::kOffAcc);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::kOffBar);
     uint64_t *a_full = bars, *a_empty = bars + C::kSlots;
     uint64_t *d_full = bars + 2 * C::kSlots, *d_empty = d_full + 1, *done = d_full + 2;
@@ -253,6 +257,7 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
         const int q = warp & 3, cg = warp >> 2;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         GWaiter wait{s_abort};
+        for (int k = tid; k < C::kPk; k += 32 * kEpiW) accp[k] = 0.0;
         for (long long u = u0; u < u1; ++u) {
             const int ju = (int)(u - u0);
             const int pair = (int)(u / a.g_chunks), chunk = (int)(u % a.g_chunks);
@@ -265,7 +270,6 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
             }
             wait(d_full, (uint32_t)(ju & 1));
             tc::fence_after_sync();
-            double *out = a.part + ((size_t)pair * a.g_chunks + chunk) * Cfg<BB>::kPacked;
 #pragma unroll 1
             for (int k = 0; k < C::kChunks; ++k) {
                 int *xb = xbuf + (k & 1) * (C::kXBuf / 4);
@@ -308,8 +312,26 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
                             if (L - s >= 0) sum += xb[((L - s) * kXCols + e8) * 128 + s * BB + cc];
                         l[L] = sum;
                     }
-                    out[packed_lower<BB>(cc, n)] = split8::combine_levels(l, ecx[cc] + ecx[n]);
+                    double *acc = accp + packed_lower<BB>(cc, n);
+                    *acc = __dadd_rn(*acc, split8::combine_levels(l, ecx[cc] + ecx[n]));
                 }
+            }
+            // the last of this CTA's consecutive chunks of the pair: write the
+            // run's sum to the pair's slot (blockIdx.x minus the first CTA that
+            // holds a chunk of the pair); the CTA holding the pair's last chunk
+            // also zeroes the slots no CTA writes
+            if (u + 1 == u1 || (int)((u + 1) / a.g_chunks) != pair) {
+                bar_epi();
+                const long long G = gridDim.x, first_u = (long long)pair * a.g_chunks;
+                const int b0 = (int)(((first_u + 1) * G + units - 1) / units) - 1;
+                const int slot = (int)blockIdx.x - b0;
+                double *out = a.part + ((size_t)pair * a.g_parts + slot) * Cfg<BB>::kPacked;
+                for (int k = tid; k < C::kPk; k += 32 * kEpiW) {
+                    out[k] = accp[k];
+                    accp[k] = 0.0;
+                }
+                if (u == first_u + a.g_chunks - 1)
+                    for (int k = tid; k < (a.g_parts - slot - 1) * C::kPk; k += 32 * kEpiW) out[C::kPk + k] = 0.0;
             }
         }
     }
@@ -323,6 +345,15 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
 }
 #undef JSVD_GSTORE
 
+int grid_for(long long units) {
+    static int nsm[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && nsm[dev] == 0) cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+    const int g = (dev >= 0 && dev < 64 && nsm[dev] > 0) ? nsm[dev] : 148;
+    return units < g ? (int)units : g;
+}
+
 template <int BB>
 void launch_gram_tc_bb(const PStepArgs &a, cudaStream_t s) {
     static int nsm[64] = {};
@@ -334,12 +365,25 @@ void launch_gram_tc_bb(const PStepArgs &a, cudaStream_t s) {
     }
     const long long units = (long long)a.npairs * a.g_chunks;
     if (units <= 0) return;
-    int grid = (dev >= 0 && dev < 64 && nsm[dev] > 0) ? nsm[dev] : 148;
-    if (units < grid) grid = (int)units;
-    gram_tc<BB><<<grid, kGThreadsTc, GramCfg<BB>::kSmem, s>>>(a);
+    gram_tc<BB><<<grid_for(units), kGThreadsTc, GramCfg<BB>::kSmem, s>>>(a);
 }
 
 }  // namespace
+
+int gram_tc_parts(const PStepArgs &a) {
+    // CTA b holds units [units b / G, units (b + 1) / G); the CTA holding unit
+    // x is ceil((x + 1) G / units) - 1
+    const long long units = (long long)a.npairs * a.g_chunks;
+    if (units <= 0) return a.g_chunks;
+    const long long G = grid_for(units);
+    int parts = 1;
+    for (int p = 0; p < a.npairs; ++p) {
+        const long long f = (long long)p * a.g_chunks, l = f + a.g_chunks - 1;
+        const long long bf = ((f + 1) * G + units - 1) / units - 1, bl = ((l + 1) * G + units - 1) / units - 1;
+        parts = (int)std::max<long long>(parts, bl - bf + 1);
+    }
+    return parts;
+}
 
 void launch_gram_tc(int BB, const PStepArgs &a, cudaStream_t s) {
     switch (BB) {

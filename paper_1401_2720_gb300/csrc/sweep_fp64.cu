@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(NT) pair_jacobi(PStepArgs a) {
     const int pair = blockIdx.x;
     const int P = a.table[2 * (a.step * a.npairs + pair)];
     const int Q = a.table[2 * (a.step * a.npairs + pair) + 1];
-    jacobi_unit<BB, NT, RT>(a.part + (size_t)pair * a.g_chunks * Cfg<BB>::kPacked, a.g_chunks, a.inner, P, Q, a.b,
+    jacobi_unit<BB, NT, RT>(a.part + (size_t)pair * a.g_parts * Cfg<BB>::kPacked, a.g_parts, a.inner, P, Q, a.b,
                     a.nplus, a.bord_lo, a.bord_hi, a.inner_sweeps, a.eps, a.vprime + (size_t)pair * BB * BB, a.vflag + pair,
                     a.counters, smem, a.split ? a.bslice + (size_t)pair * 2 * split_b_elems<BB>() : nullptr,
                     a.split ? a.bexp + (size_t)pair * 2 * BB : nullptr, a.split ? a.dexp + (size_t)pair * BB : nullptr,

@@ -48,7 +48,9 @@ struct PStepArgs {
     int fp32;               // 1: G, V are float; Gram sums and update in FP32
     double eps;             // unit roundoff of the relative test: 2^-53, or 2^-24 in FP32 sweeps
     double *part;           // Gram partials [npairs][g_chunks][BB*(BB+1)/2]
-    int g_chunks;           // g_rows / kGramRows
+    int g_chunks;           // g_rows / kGramRows (kGramRowsSplit for the split forms)
+    int g_parts;            // partial slots per pair the Jacobi kernel sums: g_chunks, or fewer when the
+                            // tcgen05 Gram adds up each CTA's consecutive chunks of a pair
     double *vprime;         // V' [npairs][BB*BB], column-major
     int *vflag;             // [npairs]: 1 if V' != I
     unsigned long long *counters;  // kCnt* slots
@@ -76,6 +78,8 @@ void launch_split_phase(int BB, Phase ph, const PStepArgs &a, cudaStream_t s);
 void launch_update_tc(int BB, const PStepArgs &a, cudaStream_t s);
 // The Gram partials on tcgen05 (gram_tc.cu), when PStepArgs::tc is set.
 void launch_gram_tc(int BB, const PStepArgs &a, cudaStream_t s);
+// Partial slots per pair the tcgen05 Gram writes for these arguments (g_parts).
+int gram_tc_parts(const PStepArgs &a);
 // gexp[j] = exponent bound of column j of G (rows [0, rows)), one CTA per column.
 void launch_col_maxexp(const double *G, int ldg, int rows, int ncols, int *gexp, cudaStream_t s);
 
