@@ -47,7 +47,7 @@ def _time_batch(mats, b, device, repeats: int, strategy: str = "rR") -> float:
     return best
 
 
-def tune(mats, candidates=(8, 16, 32), sample: int = 64, repeats: int = 2, seed: int = 0,
+def tune(mats, candidates=(8, 16, 32), sample: int = 64, repeats: int = 3, seed: int = 0,
          path: str | None = None, device=None) -> dict[int, int]:
     """{bucket index: fastest b} for the buckets that `mats` populate."""
     device = torch.device(device or "cuda")
@@ -64,7 +64,11 @@ def tune(mats, candidates=(8, 16, 32), sample: int = 64, repeats: int = 2, seed:
             continue
         pick = [group[i] for i in rng.choice(len(group), size=min(sample, len(group)), replace=False)]
         times = {b: _time_batch(pick, b, device, repeats) for b in candidates}
-        table[k] = min(times, key=times.get)
+        # the largest width within 5 % of the fastest: in the whole batch a
+        # larger b also means fewer lock-step p-steps per sweep, which a
+        # bucket timed alone does not see
+        fastest = min(times.values())
+        table[k] = max(b for b, t in times.items() if t <= 1.05 * fastest)
     _cache[name] = table
     if path:
         data = json.load(open(path)) if os.path.exists(path) else {}
