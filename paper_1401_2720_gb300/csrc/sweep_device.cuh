@@ -14,6 +14,7 @@
 
 #include <cstdint>
 
+#include "cluster_sync.cuh"
 #include "rotation.cuh"
 #include "split8.cuh"
 #include "split_mma.cuh"
@@ -250,11 +251,21 @@ __device__ __forceinline__ void rot_apply_t(RT &x, RT &y, bool hyperbolic, RT cs
     }
 }
 
-template <int BB, typename RT = double>
+//
+// CLUSTER: the CTA of rank 0 of a 2-CTA cluster runs the R side, the CTA of
+// rank 1 (another SM) the V' side (without: both sides in this CTA): the
+// R side stores each step's parameters into the peer's slots (distributed
+// shared memory) and arrives on the peer's mbarrier full[slot]; the V' side
+// waits on it and, once it has read the slot, arrives on the R side's
+// empty[slot].  Same arithmetic, so the same R and V' bit for bit.  Waits are
+// bounded (~2 s); one that gives up raises the error flag in *err.
+template <int BB, typename RT = double, bool CLUSTER = false>
 __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsigned char *tab, int P, int Q,
                                                        int b, int nplus, int bord_lo, int bord_hi, double c_eps,
                                                        double c_eps2,
-                                                       int &my_rot, int &my_proper, int &changed) {
+                                                       int &my_rot, int &my_proper, int &changed,
+                                                       uint64_t *full = nullptr, uint64_t *empty = nullptr,
+                                                       unsigned long long *err = nullptr) {
     using C = Cfg<BB>;
     constexpr int NH = C::kJacThreads;        // threads per side
     constexpr int NT = 2 * NH;
@@ -262,7 +273,16 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsig
     __shared__ double s_cs[2][NP], s_tn[2][NP];
     __shared__ int s_fl[2][NP];               // bit 0: rotate, 1: swap, 2: hyperbolic, 3: cs != 1
     const int tid = threadIdx.x;
-    if (tid < NH) {
+    const int role = CLUSTER ? (int)cl::rank() : -1;
+    bool dead = false;
+    auto cwait = [&](uint64_t *bar, uint32_t parity) {
+        if (dead) return;
+        if (!cl::wait_parity(bar, parity, 2048)) {
+            dead = true;
+            atomicOr(err, 4ull);
+        }
+    };
+    if (tid < NH && role != 1) {
         // ---------------- R side ----------------
         const int y = tid / C::kLanesPerPair;
         const int g = tid % C::kLanesPerPair;
@@ -319,15 +339,26 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsig
                 proper = rf.cs != 1.0f;
                 rot = Rot{(double)rf.cs, (double)rf.tn};
             }
-            if (st >= 2) {
-                if (slot) nbar_sync<jb::kEmpty0 + 1, NT>(); else nbar_sync<jb::kEmpty0, NT>();
+            const int flags = (rho ? 1 : 0) | (swap ? 2 : 0) | (hyp ? 4 : 0) | (proper ? 8 : 0);
+            if constexpr (!CLUSTER) {
+                if (st >= 2) {
+                    if (slot) nbar_sync<jb::kEmpty0 + 1, NT>(); else nbar_sync<jb::kEmpty0, NT>();
+                }
+                if (g == 0) {
+                    s_cs[slot][y] = rot.cs;
+                    s_tn[slot][y] = rot.tn;
+                    s_fl[slot][y] = flags;
+                }
+                if (slot) nbar_arrive<jb::kFull0 + 1, NT>(); else nbar_arrive<jb::kFull0, NT>();
+            } else {
+                if (st >= 2) cwait(&empty[slot], (uint32_t)(((st >> 1) - 1) & 1));
+                if (g == 0 && !dead) {
+                    cl::st_f64(cl::peer_addr(&s_cs[slot][y], 1), rot.cs);
+                    cl::st_f64(cl::peer_addr(&s_tn[slot][y], 1), rot.tn);
+                    cl::st_s32(cl::peer_addr(&s_fl[slot][y], 1), flags);
+                    cl::arrive_remote(cl::peer_addr(&full[slot], 1));
+                }
             }
-            if (g == 0) {
-                s_cs[slot][y] = rot.cs;
-                s_tn[slot][y] = rot.tn;
-                s_fl[slot][y] = (rho ? 1 : 0) | (swap ? 2 : 0) | (hyp ? 4 : 0) | (proper ? 8 : 0);
-            }
-            if (slot) nbar_arrive<jb::kFull0 + 1, NT>(); else nbar_arrive<jb::kFull0, NT>();
             if (rho || swap) {
 #pragma unroll
                 for (int k = 0; k < C::kRowsPerLane; ++k) {
@@ -348,7 +379,7 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsig
             }
             nbar_sync<jb::kRSide, NH>();
         }
-    } else {
+    } else if (tid >= NH && role != 0) {
         // ---------------- V' side ----------------
         const int v = tid - NH;
         const int y = v / C::kLanesPerPair;
@@ -357,13 +388,23 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsig
             const int slot = st & 1;
             const int p = tab[2 * (st * (BB / 2) + y)];
             const int q = tab[2 * (st * (BB / 2) + y) + 1];
-            if (slot) nbar_sync<jb::kFull0 + 1, NT>(); else nbar_sync<jb::kFull0, NT>();
+            if constexpr (!CLUSTER) {
+                if (slot) nbar_sync<jb::kFull0 + 1, NT>(); else nbar_sync<jb::kFull0, NT>();
+            } else {
+                cwait(&full[slot], (uint32_t)((st >> 1) & 1));
+            }
             const double cs = s_cs[slot][y], tn = s_tn[slot][y];
-            const int fl = s_fl[slot][y];
+            const int fl = dead ? 0 : s_fl[slot][y];
             if (st + 2 < BB - 1) {
-                if (slot) nbar_arrive<jb::kEmpty0 + 1, NT>(); else nbar_arrive<jb::kEmpty0, NT>();
+                if constexpr (!CLUSTER) {
+                    if (slot) nbar_arrive<jb::kEmpty0 + 1, NT>(); else nbar_arrive<jb::kEmpty0, NT>();
+                } else {
+                    __syncwarp();
+                    if ((tid & 31) == 0 && !dead) cl::arrive_remote(cl::peer_addr(&empty[slot], 0));
+                }
             }
             const bool rho = fl & 1, swap = fl & 2, hyp = fl & 4, proper = fl & 8;
+            if (role == 1 && (rho || swap)) changed = 1;
             const RT cs_t = (RT)cs, tn_t = (RT)tn;
             RT *wp = A + p * C::kLd, *wq = A + q * C::kLd;
             if (rho || swap) {
@@ -402,7 +443,7 @@ __device__ __forceinline__ void jacobi_sweep_pipelined(RT *A, RT *B, const unsig
 // of the pair's columns of G are reset (the split update recomputes them).  Global columns in [bord_lo, bord_hi) are the
 // identity border: they are exactly orthogonal to everything, and they are
 // neither rotated nor swapped, so they keep their positions.
-template <int BB, int NT = Cfg<BB>::kJacThreads, typename RT = double>
+template <int BB, int NT = Cfg<BB>::kJacThreads, typename RT = double, bool CLUSTER = false>
 __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int chunks,
                                             const unsigned char *__restrict__ inner, int P, int Q, int b,
                                             int nplus, int bord_lo, int bord_hi, int inner_sweeps, double eps,
@@ -425,83 +466,102 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     const int tid = threadIdx.x;
     for (int e = tid; e < (BB - 1) * BB; e += NT) tab[e] = inner[e];
     if (tid == 0) { s_off = 0ull; s_brk = 0; s_cnt[0] = 0; s_cnt[1] = 0; }
-
-    // (1) H = sum of the row-chunk partials in a fixed order: chunk c goes to
-    // accumulator c mod 8 (in increasing c), then the 8 accumulators are added
-    // pairwise; short dependency chains keep the FP64 latency off the path
-    for (int e = tid; e < BB * BB; e += NT) {
-        const int i = e % BB, j = e / BB;
-        if (i < j) continue;
-        const int k = packed_lower<BB>(i, j);
-        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        int c = 0;
-        for (; c + 8 <= chunks; c += 8) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] = __dadd_rn(acc[u], part[(size_t)(c + u) * C::kPacked + k]);
+    // CLUSTER: a 2-CTA cluster per pivot pair, CTA 0 the factorization and
+    // the R side of the inner sweep, CTA 1 the V' side and the V' outputs
+    const int role = CLUSTER ? (int)cl::rank() : -1;
+    __shared__ uint64_t s_full[2], s_empty[2];
+    if constexpr (CLUSTER) {
+        if (tid == 0) {
+            for (int i = 0; i < 2; ++i) {
+                tc::mbar_init(&s_full[i], BB / 2);
+                tc::mbar_init(&s_empty[i], C::kJacThreads / 32);
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (c + u < chunks) acc[u] = __dadd_rn(acc[u], part[(size_t)(c + u) * C::kPacked + k]);
-        A[i + j * C::kLd] = __dadd_rn(__dadd_rn(__dadd_rn(acc[0], acc[1]), __dadd_rn(acc[2], acc[3])),
-                                      __dadd_rn(__dadd_rn(acc[4], acc[5]), __dadd_rn(acc[6], acc[7])));
+        cl::sync();
     }
-    __syncthreads();
 
-    // (2) normalized off-diagonal maximum of H, max |h_ij| / sqrt(h_ii h_jj)
-    // (reported only): B[j] = 1/sqrt(h_jj) first, then two products per entry
-    for (int j = tid; j < BB; j += NT) {
-        const double d = A[j + j * C::kLd];
-        B[j] = d > 0.0 ? rsqrt(d) : 0.0;
-        hdiag[j] = d;
-    }
-    __syncthreads();
-    {
-        double mx = 0.0;
+    if (role != 1) {
+        // (1) H = sum of the row-chunk partials in a fixed order: chunk c goes to
+        // accumulator c mod 8 (in increasing c), then the 8 accumulators are added
+        // pairwise; short dependency chains keep the FP64 latency off the path
         for (int e = tid; e < BB * BB; e += NT) {
             const int i = e % BB, j = e / BB;
-            if (i <= j) continue;
-            mx = fmax(mx, fabs(A[i + j * C::kLd]) * B[i] * B[j]);
+            if (i < j) continue;
+            const int k = packed_lower<BB>(i, j);
+            double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            int c = 0;
+            for (; c + 8 <= chunks; c += 8) {
+    #pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = __dadd_rn(acc[u], part[(size_t)(c + u) * C::kPacked + k]);
+            }
+    #pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c + u < chunks) acc[u] = __dadd_rn(acc[u], part[(size_t)(c + u) * C::kPacked + k]);
+            A[i + j * C::kLd] = __dadd_rn(__dadd_rn(__dadd_rn(acc[0], acc[1]), __dadd_rn(acc[2], acc[3])),
+                                          __dadd_rn(__dadd_rn(acc[4], acc[5]), __dadd_rn(acc[6], acc[7])));
         }
-        atomicMax(&s_off, (unsigned long long)__double_as_longlong(mx));
-    }
-
-    // (3) Cholesky H = L L^T without pivoting (Sec. 4.1), right-looking:
-    // entry (i, j) receives -L(i,k) L(j,k) for k = 0, 1, ... in order, then the
-    // division by the pivot.  A non-positive pivot zeroes its column.  The
-    // pivot of column k + 1 is taken by thread 0, which performs that entry's
-    // last update itself (e = 0 of the trailing update), right after it.
-    auto pivot = [&](int k) {
-        const double d = A[k + k * C::kLd];
-        if (d > 0.0) {
-            s_piv = __dsqrt_rn(d);
-        } else {
-            s_piv = 0.0;
-            s_brk += 1;
-        }
-    };
-    if (tid == 0) pivot(0);
-    __syncthreads();
-    for (int k = 0; k < BB; ++k) {
-        const double piv = s_piv;
-        for (int i = k + tid; i < BB; i += NT)
-            A[i + k * C::kLd] = (piv > 0.0) ? (i == k ? piv : __ddiv_rn(A[i + k * C::kLd], piv)) : 0.0;
         __syncthreads();
-        const int rem = BB - 1 - k;
-        for (int e = tid; e < rem * rem; e += NT) {
-            const int i = k + 1 + e % rem, j = k + 1 + e / rem;
-            if (i >= j)
-                A[i + j * C::kLd] = __fma_rn(-A[i + k * C::kLd], A[j + k * C::kLd], A[i + j * C::kLd]);
-        }
-        if (tid == 0 && k + 1 < BB) pivot(k + 1);
-        __syncthreads();
-    }
 
+        // (2) normalized off-diagonal maximum of H, max |h_ij| / sqrt(h_ii h_jj)
+        // (reported only): B[j] = 1/sqrt(h_jj) first, then two products per entry
+        for (int j = tid; j < BB; j += NT) {
+            const double d = A[j + j * C::kLd];
+            B[j] = d > 0.0 ? rsqrt(d) : 0.0;
+            hdiag[j] = d;
+            if (role == 0) cl::st_f64(cl::peer_addr(&hdiag[j], 1), d);
+        }
+        __syncthreads();
+        {
+            double mx = 0.0;
+            for (int e = tid; e < BB * BB; e += NT) {
+                const int i = e % BB, j = e / BB;
+                if (i <= j) continue;
+                mx = fmax(mx, fabs(A[i + j * C::kLd]) * B[i] * B[j]);
+            }
+            atomicMax(&s_off, (unsigned long long)__double_as_longlong(mx));
+        }
+
+        // (3) Cholesky H = L L^T without pivoting (Sec. 4.1), right-looking:
+        // entry (i, j) receives -L(i,k) L(j,k) for k = 0, 1, ... in order, then the
+        // division by the pivot.  A non-positive pivot zeroes its column.  The
+        // pivot of column k + 1 is taken by thread 0, which performs that entry's
+        // last update itself (e = 0 of the trailing update), right after it.
+        auto pivot = [&](int k) {
+            const double d = A[k + k * C::kLd];
+            if (d > 0.0) {
+                s_piv = __dsqrt_rn(d);
+            } else {
+                s_piv = 0.0;
+                s_brk += 1;
+            }
+        };
+        if (tid == 0) pivot(0);
+        __syncthreads();
+        for (int k = 0; k < BB; ++k) {
+            const double piv = s_piv;
+            for (int i = k + tid; i < BB; i += NT)
+                A[i + k * C::kLd] = (piv > 0.0) ? (i == k ? piv : __ddiv_rn(A[i + k * C::kLd], piv)) : 0.0;
+            __syncthreads();
+            const int rem = BB - 1 - k;
+            for (int e = tid; e < rem * rem; e += NT) {
+                const int i = k + 1 + e % rem, j = k + 1 + e / rem;
+                if (i >= j)
+                    A[i + j * C::kLd] = __fma_rn(-A[i + k * C::kLd], A[j + k * C::kLd], A[i + j * C::kLd]);
+            }
+            if (tid == 0 && k + 1 < BB) pivot(k + 1);
+            __syncthreads();
+        }
+
+    }
     // (4) R = L^T into B; V' = I into A (both in RT from here on)
     RT *Rt = reinterpret_cast<RT *>(B);
     RT *Vt = reinterpret_cast<RT *>(A);
-    for (int e = tid; e < BB * BB; e += NT) {
-        const int i = e % BB, j = e / BB;
-        Rt[i + j * C::kLd] = (i <= j) ? (RT)A[j + i * C::kLd] : (RT)0;
+    if (role != 1) {
+        for (int e = tid; e < BB * BB; e += NT) {
+            const int i = e % BB, j = e / BB;
+            Rt[i + j * C::kLd] = (i <= j) ? (RT)A[j + i * C::kLd] : (RT)0;
+        }
     }
     __syncthreads();
     for (int e = tid; e < BB * BB; e += NT) {
@@ -517,8 +577,9 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     if constexpr (NT == 2 * C::kJacThreads) {
         // one inner sweep, V' rotated one step behind R by the second half of
         // the threads
-        jacobi_sweep_pipelined<BB, RT>(Vt, Rt, tab, P, Q, b, nplus, bord_lo, bord_hi, c_eps, c_eps2, my_rot, my_proper,
-                                       changed);
+        jacobi_sweep_pipelined<BB, RT, CLUSTER>(Vt, Rt, tab, P, Q, b, nplus, bord_lo, bord_hi, c_eps, c_eps2, my_rot,
+                                             my_proper,
+                                       changed, s_full, s_empty, &counters[kCntErr]);
         sweeps_done = 1;
     } else {
     static_assert(NT == C::kJacThreads && sizeof(RT) == sizeof(double), "thread count, FP64 inner sweep");
@@ -585,29 +646,38 @@ __device__ __forceinline__ void jacobi_unit(const double *__restrict__ part, int
     }
     }
 
-    // (6) V' and its flag to global memory; counters
+    // (6) V' and its flag to global memory; counters (in a cluster: the V'
+    // outputs from CTA 1, the rotation counters from CTA 0)
     const int any_change = __syncthreads_or(changed);
-    for (int e = tid; e < BB * BB; e += NT) {
-        const int i = e % BB, j = e / BB;
-        vp[e] = (double)Vt[i + j * C::kLd];
+    if (role != 0) {
+        for (int e = tid; e < BB * BB; e += NT) {
+            const int i = e % BB, j = e / BB;
+            vp[e] = (double)Vt[i + j * C::kLd];
+        }
+        if constexpr (sizeof(RT) == sizeof(double))
+            if (bsl && any_change) split_right_factor<BB, NT>(A, hdiag, dx, bsl, bexp, dexp, tc);
+        // the update of G rewrites these columns and max-reduces their new bounds
+        if (gexp && any_change)
+            for (int k = tid; k < BB; k += NT) gexp[block_col(P, Q, b, k)] = split::kNoExp;
     }
-    if constexpr (sizeof(RT) == sizeof(double))
-        if (bsl && any_change) split_right_factor<BB, NT>(A, hdiag, dx, bsl, bexp, dexp, tc);
-    // the update of G rewrites these columns and max-reduces their new bounds
-    if (gexp && any_change)
-        for (int k = tid; k < BB; k += NT) gexp[block_col(P, Q, b, k)] = split::kNoExp;
     atomicAdd(&s_cnt[0], my_rot);
     atomicAdd(&s_cnt[1], my_proper);
     __syncthreads();
     if (tid == 0) {
-        *vflag = any_change;
-        atomicAdd(&counters[kCntRot], (unsigned long long)s_cnt[0]);
-        atomicAdd(&counters[kCntProper], (unsigned long long)s_cnt[1]);
-        if (any_change) atomicAdd(&counters[kCntUpdated], 1ull);
-        atomicAdd(&counters[kCntInner], (unsigned long long)sweeps_done);
-        if (s_brk) atomicAdd(&counters[kCntBreak], (unsigned long long)s_brk);
-        atomicMax(&counters[kCntOff], s_off);
+        if (role != 0) {
+            *vflag = any_change;
+            if (any_change) atomicAdd(&counters[kCntUpdated], 1ull);
+        }
+        if (role != 1) {
+            atomicAdd(&counters[kCntRot], (unsigned long long)s_cnt[0]);
+            atomicAdd(&counters[kCntProper], (unsigned long long)s_cnt[1]);
+            atomicAdd(&counters[kCntInner], (unsigned long long)sweeps_done);
+            if (s_brk) atomicAdd(&counters[kCntBreak], (unsigned long long)s_brk);
+            atomicMax(&counters[kCntOff], s_off);
+        }
     }
+    // no CTA of the cluster may exit while its peer can still reach its shared memory
+    if constexpr (CLUSTER) cl::sync();
 }
 
 // ---------------------------------------------------------------------------

@@ -7,6 +7,45 @@
 
 namespace jsvd {
 
+// The pipelined variant on a 2-CTA cluster per pivot pair (one SM for the
+// factorization and the R side, another for the V' side and the V' outputs),
+// used when the p-step has at most half as many pairs as the GPU has SMs: the
+// R side then has its SM's FP64 pipe to itself.  Same results bit for bit.
+template <int BB, typename RT = double>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(2 * Cfg<BB>::kJacThreads)
+    pair_jacobi_cl(PStepArgs a) {
+    extern __shared__ __align__(16) double smem[];
+    const int pair = blockIdx.x >> 1;
+    const int P = a.table[2 * (a.step * a.npairs + pair)];
+    const int Q = a.table[2 * (a.step * a.npairs + pair) + 1];
+    const double *part = a.part + (size_t)pair * a.g_parts * Cfg<BB>::kPacked;
+    uint16_t *bsl = a.split ? a.bslice + (size_t)pair * 2 * split_b_elems<BB>() : nullptr;
+    int *bexp = a.split ? a.bexp + (size_t)pair * 2 * BB : nullptr;
+    int *dexp = a.split ? a.dexp + (size_t)pair * BB : nullptr;
+    int *gexp = a.split ? a.gexp : nullptr;
+    jacobi_unit<BB, 2 * Cfg<BB>::kJacThreads, RT, true>(part, a.g_parts, a.inner, P, Q, a.b, a.nplus, a.bord_lo,
+                                                         a.bord_hi, 1, a.eps, a.vprime + (size_t)pair * BB * BB,
+                                                         a.vflag + pair, a.counters, smem, bsl, bexp, dexp, gexp,
+                                                         a.tc != 0);
+}
+
+// The cluster kernel requests enough shared memory that no two of its CTAs
+// share an SM (the point is a second FP64 pipe for the V' side).
+template <int BB>
+constexpr size_t jacobi_cl_smem_bytes() {
+    return jacobi_smem_bytes<BB>() > 120 * 1024 ? jacobi_smem_bytes<BB>() : 120 * 1024;
+}
+
+// SMs of the current device (cached per device).
+static int sm_count() {
+    static int nsm[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (nsm[dev] == 0) cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+    return nsm[dev];
+}
+
 template <int BB, typename T>
 __global__ void __launch_bounds__(Cfg<BB>::kGramThreads) gram_partial(PStepArgs a) {
     extern __shared__ __align__(16) double smem[];
@@ -69,6 +108,10 @@ static void configure_once() {
                          (int)jacobi_smem_bytes<BB>());
     cudaFuncSetAttribute(pair_jacobi<BB, 2 * Cfg<BB>::kJacThreads, float>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem_bytes<BB>());
+    cudaFuncSetAttribute(pair_jacobi_cl<BB, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)jacobi_cl_smem_bytes<BB>());
+    cudaFuncSetAttribute(pair_jacobi_cl<BB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)jacobi_cl_smem_bytes<BB>());
     cudaFuncSetAttribute(block_update<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)update_smem_bytes<BB, T>());
     done[dev] = true;
@@ -86,7 +129,12 @@ static void launch_bb(Phase ph, const PStepArgs &a, cudaStream_t s) {
         }
         case Phase::Jacobi: {
             const size_t sm = jacobi_smem_bytes<BB>();
-            if (a.inner_sweeps == 1 && a.fp32)
+            const bool cluster = a.inner_sweeps == 1 && 2 * a.npairs <= sm_count();
+            if (cluster && a.fp32)
+                pair_jacobi_cl<BB, float><<<2 * a.npairs, 2 * C::kJacThreads, jacobi_cl_smem_bytes<BB>(), s>>>(a);
+            else if (cluster)
+                pair_jacobi_cl<BB, double><<<2 * a.npairs, 2 * C::kJacThreads, jacobi_cl_smem_bytes<BB>(), s>>>(a);
+            else if (a.inner_sweeps == 1 && a.fp32)
                 pair_jacobi<BB, 2 * C::kJacThreads, float><<<a.npairs, 2 * C::kJacThreads, sm, s>>>(a);
             else if (a.inner_sweeps == 1)
                 pair_jacobi<BB, 2 * C::kJacThreads><<<a.npairs, 2 * C::kJacThreads, sm, s>>>(a);
