@@ -163,3 +163,23 @@ def test_split_coherent_digits(cuda, b):
     assert info["converged"] and info["breakdowns"] == 0
     assert np.max(np.abs(_np(S) - sl)) <= 1e-13 * sl[0]
     assert _orth(_np(V)) <= 50 * n * EPS
+
+
+def test_split_gram_chunk_runs_and_cluster_jacobi(cuda):
+    """2048 x 1280, b = 32: 20 pivot pairs x 8 Gram chunks of 256 rows = 160
+    units for the GPU's CTAs, so some CTAs hold two consecutive chunks of a
+    pair and sum them before writing the pair's partial, and the 20 pairs run
+    their Jacobi steps on 2-CTA clusters.  Element-wise against the oracle
+    after one block sweep, and the converged singular values against LAPACK."""
+    m, n, b = 2048, 1280, 32
+    A = I.graded_gaussian(m, n, seed=11)
+    r = O.block_svd(A, b, strategy="rR", max_sweeps=1)
+    U, S, V, info = J.svd(_t(A, cuda), b=b, strategy="rR", max_sweeps=1, sort=False, return_info=True,
+                          contraction="split")
+    G = _np(U) * _np(S)[None, :]
+    assert_columns_close(G, r["G"])
+    assert np.max(np.abs(_np(V) - r["V"])) <= 1e-12
+    U, S, V, info = J.svd(_t(A, cuda), b=b, return_info=True, contraction="split")
+    sl = np.linalg.svd(A, compute_uv=False)
+    assert info["converged"] and info["breakdowns"] == 0
+    assert np.max(np.abs(_np(S) - sl)) <= 1e-13 * sl[0]
