@@ -1,6 +1,8 @@
 """FP64 block contractions on the tensor cores (contraction="split"): the Gram
 (Eq. (2.7)) and the block update (Eq. (2.9)) formed from exact bf16 digit
 slices.  The same parity gates as the FP64 FMA form, against the oracle."""
+import os
+
 import numpy as np
 import pytest
 
@@ -173,7 +175,11 @@ def test_split_gram_chunk_runs_and_cluster_jacobi(cuda):
     after one block sweep, and the converged singular values against LAPACK."""
     m, n, b = 2048, 1280, 32
     A = I.graded_gaussian(m, n, seed=11)
-    r = O.block_svd(A, b, strategy="rR", max_sweeps=1)
+    O.set_threads(os.cpu_count() or 1)      # disjoint pairs: bitwise the same as one thread
+    try:
+        r = O.block_svd(A, b, strategy="rR", max_sweeps=1)
+    finally:
+        O.set_threads(1)
     U, S, V, info = J.svd(_t(A, cuda), b=b, strategy="rR", max_sweeps=1, sort=False, return_info=True,
                           contraction="split")
     G = _np(U) * _np(S)[None, :]
