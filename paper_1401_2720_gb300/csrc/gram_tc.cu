@@ -25,7 +25,7 @@
 // units.  Warp roles, synchronised through shared-memory mbarriers:
 //   warps 0-15  epilogue (TMEM lane quadrant w % 4, level blocks 2 (w / 4),
 //               2 (w / 4) + 1 in the drain; one output each in the combine);
-//   warps 16-23 producers: thread (column c, 8-row octet o) splits 8 entries
+//   warps 16-23 producers: thread (column c, 8-row octet o; lanes along c) splits 8 entries
 //               of each round (2048 / BB rows) into digits and stores them in
 //               both operand layouts (the B layout is the A layout's rows
 //               regrouped by output-column half);
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
     if (warp == kMmaW) tc::tmem_alloc(s_tmem, C::kTmemCols);
     if (tid == 0) {
         for (int i = 0; i < C::kSlots; ++i) {
-            tc::mbar_init(&a_full[i], kProdW);
+            tc::mbar_init(&a_full[i], kProdW / C::kRoundKS);   // the warps that write one K-step
             tc::mbar_init(&a_empty[i], 1);
         }
         tc::mbar_init(d_full, 1);
@@ -189,7 +189,9 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
     } else if (warp >= kProdW0) {
         // ---------------- producers ----------------------------------------------
         const int pt = tid - 32 * kProdW0;
-        const int c = pt / C::kOct, o = pt % C::kOct;
+        // consecutive lanes take consecutive columns of one octet, so the 8 lanes
+        // of a 16-byte store phase fill one 128-byte row chunk (no bank conflicts)
+        const int c = pt % BB, o = pt / BB;
         const int ksr = o >> 1, kk = (o & 1) * 8;
         const uint32_t offA = (uint32_t)(ksr * C::kStage) + tc::op_offset(c, kk);
         const uint32_t offB = (uint32_t)(ksr * C::kStage + C::kABytes + (c / C::kNC) * C::kBHalf) +
@@ -244,8 +246,8 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
                     tc::fence_proxy_async();
                 }
                 __syncwarp();
-                if (lane == 0 && !wait.dead)
-                    for (int kr = 0; kr < C::kRoundKS; ++kr) tc::mbar_arrive(&a_full[slot0 + kr]);
+                // a warp's lanes share one octet pair, hence one K-step of the round
+                if (lane == 0 && !wait.dead) tc::mbar_arrive(&a_full[slot0 + ksr]);
                 if (more) {
 #pragma unroll
                     for (int v = 0; v < 4; ++v) cur[v] = nxt[v];
