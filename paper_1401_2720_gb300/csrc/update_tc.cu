@@ -16,11 +16,12 @@
 //   warps 16-23 producers: thread (row r, column half) makes two passes over
 //               its row's entries (L1/L2 resident after the first): the row's
 //               exponent bound (max over the row, through shared memory), then
-//               the 8 digit slices of its K-steps, 8 entries at a time.
-//               Warp 16 also allocates TMEM, and after writing its own stages
-//               of a tile its lane 0 copies the pair's right-factor image into
-//               shared memory (cp.async.bulk, when the pair changes) and
-//               issues the tile's MMAs.
+//               the 8 digit slices of its K-steps, 8 entries at a time.  The
+//               first pass needs no stage, so it overlaps the MMAs still
+//               reading the previous tile's stages;
+//   warp 24     allocates TMEM; its lane 0 copies the pair's right-factor
+//               image into shared memory (cp.async.bulk, when the pair
+//               changes) and issues every tile's MMAs as its stages fill.
 // Per tile and output-column half h (BB = 64: two halves of 32 columns;
 // BB <= 32: one), for every K-step of 16 and slice i = 0..7 one MMA
 //   D[32 (8 levels) ... ] += A_i (128 x 16) x [B_0 .. B_{7-i}]^T
@@ -39,8 +40,8 @@ namespace jsvd {
 
 namespace {
 
-constexpr int kEpiWarps = 16, kProdWarp0 = 16, kProdWarps = 8, kMmaWarp = kProdWarp0;
-constexpr int kTcThreads = 32 * (kEpiWarps + kProdWarps);        // 768
+constexpr int kEpiWarps = 16, kProdWarp0 = 16, kProdWarps = 8, kMmaWarp = kProdWarp0 + kProdWarps;
+constexpr int kTcThreads = 32 * (kEpiWarps + kProdWarps + 1);    // 800
 constexpr int kTileRows = 128;
 constexpr int kBarProd = 1, kBarEpi = 2;                         // named barriers
 
@@ -171,8 +172,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_tc(PStepArgs a) {
     const long long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
 
     if (warp >= kProdWarp0) {
-        // ---------------- producers ----------------------------------------------
-        const int pt = tid - 32 * kProdWarp0;
+        // ---------------- producers and the MMA warp -----------------------------
+        const int pt = tid - 32 * kProdWarp0;    // producers: 0 .. 255
         const int r = pt & 127, ch = pt >> 7;
         const int c0 = ch * U::kCPT;
         Waiter wait{s_abort};
@@ -246,7 +247,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_tc(PStepArgs a) {
                 if (!wait.dead) tc::mma_commit(&B.d_full[buf]);
             }
         };
-        for (long long t = t0; t < t1; ++t) {
+        if (warp == kMmaWarp) {
+            if (issuer) {
+                for (long long t = t0; t < t1; ++t) issue_tile(t);
+                if (m_issued) {
+                    // drain: nothing may still write TMEM when it is freed (<= ~2 s)
+                    tc::mma_commit(B.b_free);
+                    tc::mbar_wait(B.b_free, (uint32_t)(m_frees & 1), 2048, 1000000);
+                }
+            }
+            __syncwarp();
+        } else for (long long t = t0; t < t1; ++t) {
             const int j = (int)(t - t0);
             int pair, ver;
             size_t row0;
@@ -255,13 +266,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_tc(PStepArgs a) {
             // the column scales of this tile's version (0 for V)
             int *dx = dxs + (j & 1) * BB;
             for (int k = pt; k < BB; k += 32 * kProdWarps) dx[k] = ver ? 0 : a.dexp[(size_t)pair * BB + k];
-            // the stages this thread writes must be free
-#pragma unroll
-            for (int g = 0; g < U::kCPT / 8; ++g) {
-                const int col = c0 + 8 * g;
-                const int s = j * KS + col / 16, slot = s % U::kASlots, use = s / U::kASlots;
-                if ((col % 16 == 0 || g == 0) && use >= 1) wait(&B.a_empty[slot], (uint32_t)((use - 1) & 1));
-            }
             asm volatile("bar.sync %0, %1;" ::"n"(kBarProd), "n"(32 * kProdWarps) : "memory");
             // the next tile's entries of this thread into L2, so that neither
             // of its passes waits on HBM
@@ -303,16 +307,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_tc(PStepArgs a) {
                     if (lane == 0) tc::mbar_arrive(&B.r_full[j & 1]);
                 }
             }
+            // the stages this thread writes must be free (the MMAs of the
+            // previous tile read them while the first pass ran)
+#pragma unroll
+            for (int g = 0; g < U::kCPT / 8; ++g) {
+                const int col = c0 + 8 * g;
+                const int s = j * KS + col / 16, slot = s % U::kASlots, use = s / U::kASlots;
+                if ((col % 16 == 0 || g == 0) && use >= 1) wait(&B.a_empty[slot], (uint32_t)((use - 1) & 1));
+            }
+            // second pass, 8 entries at a time; the next 8 are loaded before
+            // this group's digits are stored (and its stage published)
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = src[u * ldx];
 #pragma unroll
             for (int g = 0; g < U::kCPT / 8; ++g) {
                 const int col = c0 + 8 * g;
                 const int ks = col / 16, kk = col % 16;
                 const int slot = (j * KS + ks) % U::kASlots;
                 const bool last = kk == 8 || 8 * g + 8 == U::kCPT;
-                if (wait.dead) continue;
                 unsigned long long z[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) z[u] = split8::fixed_biased(src[(8 * g + u) * ldx], -dx[col + u], E);
+                for (int u = 0; u < 8; ++u) z[u] = split8::fixed_biased(v[u], -dx[col + u], E);
+                if (8 * g + 8 < U::kCPT) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = src[(8 * g + 8 + u) * ldx];
+                }
+                if (wait.dead) continue;
                 split8::store_digits8(As + slot * U::kASlotBytes + tc::op_offset(r, kk), 4096, z);
                 if (last) {
                     tc::fence_proxy_async();
@@ -320,13 +341,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_tc(PStepArgs a) {
                     if (lane == 0) tc::mbar_arrive(&B.a_full[slot]);
                 }
             }
-            if (issuer) issue_tile(t);
             __syncwarp();
-        }
-        if (issuer && m_issued) {
-            // drain: nothing may still write TMEM when it is freed (<= ~2 s)
-            tc::mma_commit(B.b_free);
-            tc::mbar_wait(B.b_free, (uint32_t)(m_frees & 1), 2048, 1000000);
         }
     } else {
         // ---------------- epilogue (warps 0-15: TMEM lane quadrant w % 4, column quarter w / 4) ----
