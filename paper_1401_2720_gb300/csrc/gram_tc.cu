@@ -15,16 +15,19 @@
 // j + s.  For BB = 64 this is 4 MMAs per K-step and half (N = 256, 192, 128,
 // 64: 11 % more digit products than the 36 needed, at the full M = 128 rate).
 // Every TMEM column accumulates at most 8 / SF slices over 256 rows, so its
-// sums are integers below 2^24 and exact in FP32.  The epilogue reads the
-// columns of 8 output columns at a time into shared memory as ints, adds the
-// SF parts of every level, recombines (split8::combine_levels, one rounding)
-// and writes the lower triangle of the partial (the layout of the other Gram
-// forms: [pair][chunk][packed lower]).
+// sums are integers below 2^24 and exact in FP32.  The epilogue converts
+// them to ints and adds the parts of every level of the lower triangle into
+// integer level sums in shared memory, which then hold the exact level sums
+// of all the CTA's consecutive chunks of the pair; it recombines them
+// (split8::combine_levels, one rounding) once per such run and writes the
+// run's partial (layout [pair][slot][packed lower]; a slot per CTA holding
+// chunks of the pair).
 //
 // One persistent CTA per SM walks a contiguous range of the (pair, chunk)
 // units.  Warp roles, synchronised through shared-memory mbarriers:
-//   warps 0-15  epilogue (TMEM lane quadrant w % 4, level blocks 2 (w / 4),
-//               2 (w / 4) + 1 in the drain; one output each in the combine);
+//   warps 0-15  epilogue (TMEM lane quadrant w % 4, every fourth 16-column
+//               load from w / 4 in the drain; outputs tid, tid + 512, ... in
+//               the recombination);
 //   warps 16-23 producers: thread (column c, 8-row octet o; lanes along c) splits 8 entries
 //               of each round (2048 / BB rows) into digits and stores them in
 //               both operand layouts (the B layout is the A layout's rows
@@ -47,7 +50,7 @@ constexpr int kEpiW = 16, kProdW0 = 16, kProdW = 8, kMmaW = 24;
 constexpr int kGThreadsTc = 32 * (kEpiW + kProdW + 1);  // 800
 constexpr int kBarEpiG = 3;                            // named barrier of the epilogue warps
 constexpr int kStageBytesTotal = 128 * 1024;           // operand stages
-constexpr int kXCols = 8;                              // output columns per epilogue chunk
+constexpr int kMaxRun = 32;                            // chunks whose level sums stay below 2^30
 
 template <int BB> struct GramCfg {
     static constexpr int kSF = 128 / BB;               // slices stacked along M: 2, 4, 8
@@ -65,12 +68,11 @@ template <int BB> struct GramCfg {
     static constexpr int kRoundRows = 8 * kOct;        // 32, 64, 128
     static constexpr int kRoundKS = kRoundRows / 16;   // 2, 4, 8
     static constexpr int kRounds = kGramRowsSplit / kRoundRows;       // 8, 4, 2
-    static constexpr int kChunks = BB / kXCols;        // epilogue chunks: 8, 4, 2
-    static constexpr int kXBuf = 8 * kXCols * 128 * 4; // one drain buffer: 32 KB
-    static constexpr int kOffX = kStageBytesTotal;
-    static constexpr int kOffE = kOffX + 2 * kXBuf;    // int [BB]: the unit's column exponents (epilogue)
     static constexpr int kPk = BB * (BB + 1) / 2;      // outputs (packed lower triangle)
-    static constexpr int kOffAcc = kOffE + BB * 4;     // double [kPk]: the run's sum over its chunks
+    static constexpr int kTmemChunks = kTmemCols / 16; // 16-column TMEM loads of a unit: 32, 16, 8
+    static constexpr int kOffLev = kStageBytesTotal;   // int [8][kPk]: the run's level sums
+    static constexpr int kOffE = kOffLev + 8 * kPk * 4;    // int [BB]: the unit's column exponents (epilogue)
+    static constexpr int kOffAcc = kOffE + BB * 4;     // double [kPk]: the run's sum over its flushes
     static constexpr int kOffBar = kOffAcc + kPk * 8;  // a_full[kSlots], a_empty[kSlots], d_full, d_empty, done
     static constexpr int kNumBars = 2 * kSlots + 3;
     static constexpr int kOffMisc = kOffBar + 8 * kNumBars;           // tmem base, abort flag
@@ -120,7 +122,7 @@ template <int BB>
 __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
     using C = GramCfg<BB>;
     extern __shared__ __align__(1024) unsigned char sm[];
-    int *xbuf = reinterpret_cast<int *>(sm + C::kOffX);
+    int *lev = reinterpret_cast<int *>(sm + C::kOffLev);
     int *ecx = reinterpret_cast<int *>(sm + C::kOffE);
     double *accp = reinterpret_cast<double *>(sm + C::kOffAcc);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::kOffBar);
@@ -228,8 +230,12 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
                     const double *p = rd + 1 < C::kRounds ? src_of(u, rd + 1) : src_of(u + 1, 0);
 #pragma unroll
                     for (int v = 0; v < 4; ++v) nxt[v] = *reinterpret_cast<const double2 *>(p + 2 * v);
-                    if (rd + 2 < C::kRounds) asm volatile("prefetch.global.L2 [%0];" ::"l"(src_of(u, rd + 2)));
                 }
+                // two rounds ahead into L2, across the unit boundary as well
+                if (rd + 2 < C::kRounds)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(src_of(u, rd + 2)));
+                else if (u + 1 < u1)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(src_of(u + 1, rd + 2 - C::kRounds)));
                 const int s0 = ju * C::kKSteps + rd * C::kRoundKS;
                 const int slot0 = s0 % C::kSlots, use = s0 / C::kSlots;
                 if (use >= 1) wait(&a_empty[slot0 + ksr], (uint32_t)((use - 1) & 1));
@@ -256,84 +262,98 @@ __global__ void __launch_bounds__(kGThreadsTc, 1) gram_tc(PStepArgs a) {
         }
     } else {
         // ---------------- epilogue (warps 0-15) -----------------------------------
+        // Every chunk of a pair has the same column scales, so the level sums
+        // of a CTA's consecutive chunks of one pair add up exactly as
+        // integers: the drain adds each unit's TMEM parts into lev (shared
+        // memory) and frees the accumulators at once; the recombination runs
+        // once per run of chunks (at most kMaxRun: per unit |lev_L| <=
+        // 7 * 2^22, as only 6 of a level's 8 digit products reach 2^14 per
+        // row, so kMaxRun units stay below 2^30, combine_levels' range).
         const int q = warp & 3, cg = warp >> 2;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        const int ln = 32 * q + lane, s_ln = ln / BB, c_ln = ln % BB;
+        // warp-uniform bounds of the lanes' stack slice and column
+        const int s_min = (32 * q) / BB, c_max = BB >= 32 ? (32 * q) % BB + 31 : BB - 1;
         GWaiter wait{s_abort};
         for (int k = tid; k < C::kPk; k += 32 * kEpiW) accp[k] = 0.0;
+        for (int k = tid; k < 8 * C::kPk; k += 32 * kEpiW) lev[k] = 0;
+        int run_len = 0;
         for (long long u = u0; u < u1; ++u) {
             const int ju = (int)(u - u0);
-            const int pair = (int)(u / a.g_chunks), chunk = (int)(u % a.g_chunks);
+            const int pair = (int)(u / a.g_chunks);
             const int P = a.table[2 * (a.step * a.npairs + pair)];
             const int Q = a.table[2 * (a.step * a.npairs + pair) + 1];
-            bar_epi();      // the previous unit's combines have read ecx
+            bar_epi();      // the previous flush has read ecx and cleared lev
             for (int k = tid; k < BB; k += 32 * kEpiW) {
                 const int e = a.gexp[gcol(P, Q, a.b, k)];
                 ecx[k] = e == split::kNoExp ? 0 : e;
             }
             wait(d_full, (uint32_t)(ju & 1));
             tc::fence_after_sync();
+            if (!wait.dead) {
+                // drain: 16-column loads cg, cg + 4, ... of this quadrant's lanes;
+                // lane (s, c) and column (half h, block j, n') hold a part of
+                // level j + s of output (c, h NC + n'), kept for c >= n, level <= 7
 #pragma unroll 1
-            for (int k = 0; k < C::kChunks; ++k) {
-                int *xb = xbuf + (k & 1) * (C::kXBuf / 4);
-                const int n0 = k * kXCols;
-                if (!wait.dead) {
-                    // drain: level blocks 2 cg, 2 cg + 1 of the chunk's columns, this quadrant's lanes
-                    const uint32_t col = (uint32_t)((n0 / C::kNC) * C::kHalfCols + n0 % C::kNC);
+                for (int k16 = cg; k16 < C::kTmemChunks; k16 += 4) {
+                    const int col0 = 16 * k16;
+                    const int h = col0 / C::kHalfCols, j = (col0 % C::kHalfCols) / C::kNC;
+                    const int n_lo = h * C::kNC + col0 % C::kNC;
+                    if (s_min + j > 7 || c_max < n_lo) continue;      // nothing kept (warp-uniform)
+                    uint32_t v[16];
+                    tc::tmem_ld16(tbase + lane_base + (uint32_t)col0, v);
+                    tc::tmem_ld_wait();
+                    const int L = j + s_ln, c = c_ln;
+                    if (L <= 7) {
+                        int *lv = lev + L * C::kPk;
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int bl = 2 * cg + j;
-                        uint32_t v[8];
-                        tc::tmem_ld8(tbase + lane_base + col + (uint32_t)(bl * C::kNC), v);
-                        tc::tmem_ld_wait();
-#pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            xb[(bl * kXCols + e) * 128 + 32 * q + lane] = __float2int_rn(__uint_as_float(v[e]));
+                        for (int e = 0; e < 16; ++e) {
+                            const int n = n_lo + e;
+                            if (c >= n) atomicAdd(lv + packed_lower<BB>(c, n), __float2int_rn(__uint_as_float(v[e])));
+                        }
                     }
-                }
-                if (k == C::kChunks - 1) {
-                    // every TMEM read of this unit is done: the next unit's MMAs may start
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0 && !wait.dead) tc::mbar_arrive(d_empty);
-                }
-                bar_epi();
-                // combine: output (c, n), c >= n, n in [n0, n0 + 8), one per thread
-                int t = tid, n = n0;
-                while (n < n0 + kXCols - 1 && t >= BB - n) {
-                    t -= BB - n;
-                    ++n;
-                }
-                if (t < BB - n && !wait.dead) {
-                    const int cc = n + t, e8 = n - n0;
-                    int l[split8::kSlices];
-#pragma unroll
-                    for (int L = 0; L < split8::kSlices; ++L) {
-                        int sum = 0;
-#pragma unroll
-                        for (int s = 0; s < C::kSF; ++s)
-                            if (L - s >= 0) sum += xb[((L - s) * kXCols + e8) * 128 + s * BB + cc];
-                        l[L] = sum;
-                    }
-                    double *acc = accp + packed_lower<BB>(cc, n);
-                    *acc = __dadd_rn(*acc, split8::combine_levels(l, ecx[cc] + ecx[n]));
                 }
             }
+            // every TMEM read of this unit is done: the next unit's MMAs may start
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0 && !wait.dead) tc::mbar_arrive(d_empty);
+            ++run_len;
             // the last of this CTA's consecutive chunks of the pair: write the
             // run's sum to the pair's slot (blockIdx.x minus the first CTA that
             // holds a chunk of the pair); the CTA holding the pair's last chunk
             // also zeroes the slots no CTA writes
-            if (u + 1 == u1 || (int)((u + 1) / a.g_chunks) != pair) {
-                bar_epi();
+            const bool run_end = u + 1 == u1 || (int)((u + 1) / a.g_chunks) != pair;
+            if (run_end || run_len == kMaxRun) {
+                bar_epi();      // every level addition of the drain is done
                 const long long G = gridDim.x, first_u = (long long)pair * a.g_chunks;
                 const int b0 = (int)(((first_u + 1) * G + units - 1) / units) - 1;
                 const int slot = (int)blockIdx.x - b0;
                 double *out = a.part + ((size_t)pair * a.g_parts + slot) * Cfg<BB>::kPacked;
                 for (int k = tid; k < C::kPk; k += 32 * kEpiW) {
-                    out[k] = accp[k];
-                    accp[k] = 0.0;
+                    int n = 0, off = 0;     // (cc, n) of packed index k
+                    while (k >= off + BB - n) {
+                        off += BB - n;
+                        ++n;
+                    }
+                    const int cc = n + (k - off);
+                    int l[split8::kSlices];
+#pragma unroll
+                    for (int L = 0; L < split8::kSlices; ++L) {
+                        l[L] = lev[L * C::kPk + k];
+                        lev[L * C::kPk + k] = 0;
+                    }
+                    const double v = wait.dead ? 0.0 : __dadd_rn(accp[k], split8::combine_levels(l, ecx[cc] + ecx[n]));
+                    if (run_end) {
+                        out[k] = v;
+                        accp[k] = 0.0;
+                    } else {
+                        accp[k] = v;
+                    }
                 }
-                if (u == first_u + a.g_chunks - 1)
+                if (run_end && u == first_u + a.g_chunks - 1)
                     for (int k = tid; k < (a.g_parts - slot - 1) * C::kPk; k += 32 * kEpiW) out[C::kPk + k] = 0.0;
+                run_len = 0;
             }
         }
     }

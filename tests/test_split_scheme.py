@@ -160,6 +160,28 @@ def _stacked_gram_levels(Dg: np.ndarray, BB: int):
     return acc, lev
 
 
+def _upper_half_gram_levels(Dg: np.ndarray):
+    """The tcgen05 Gram's half 1 for BB = 64 (outputs n >= 32, which need the
+    columns c >= 32 only): the A operand is the 4 slices 4 g .. 4 g + 3 of
+    those columns (lane 32 s + c - 32), the B operand slices 0 .. 7 - 4 g,
+    MMA g adds at column block 4 g, so lane 32 s + c', block j accumulates
+    sum_{4 g <= j} sum_k d_{4 g + s}(k, 32 + c') d_{j - 4 g}(k, n).  Returns
+    those sums [lane, block, n - 32] and the levels [c - 32, n - 32, L]."""
+    acc = np.zeros((128, 8, 32), dtype=object)
+    for g in range(2):
+        for s in range(4):
+            for j in range(4 * g, 8):
+                for c in range(32):
+                    acc[32 * s + c, j, :] += [int(Dg[4 * g + s, :, 32 + c] @ Dg[j - 4 * g, :, 32 + n])
+                                              for n in range(32)]
+    lev = np.zeros((32, 32, 8), dtype=object)
+    for L in range(8):
+        for s in range(4):
+            if L - s >= 0:
+                lev[:, :, L] += acc[32 * s:32 * (s + 1), L - s, :]
+    return acc, lev
+
+
 @pytest.mark.parametrize("BB", [16, 64])
 @pytest.mark.parametrize("kind", ["coherent", "extreme"])
 def test_stacked_gram_column_sums_exact_and_levels(BB, kind):
@@ -186,3 +208,16 @@ def test_stacked_gram_column_sums_exact_and_levels(BB, kind):
                 assert lev[c, n, L] == sum(int(Dg[i, :, c] @ Dg[L - i, :, n]) for i in range(L + 1))
     if kind == "extreme":
         assert max(abs(int(v)) for v in lev.flat) > 2 ** 24
+    # the epilogue adds the level sums of up to 32 consecutive chunks of a pair
+    # as int32 and recombines them with combine_levels (|lev| < 2^30): one
+    # chunk's levels stay within 7 2^22 (only 6 of a level's 8 digit products
+    # reach 2^14 per row, the other two hold d_0, |d_0| <= 64)
+    assert max(abs(int(v)) for v in lev.flat) <= 7 * 2 ** 22
+    assert 32 * max(abs(int(v)) for v in lev.flat) < 2 ** 30
+    if BB == 64:
+        acc1, lev1 = _upper_half_gram_levels(Dg)
+        assert max(abs(int(v)) for v in acc1.flat) <= 2 ** 23
+        for c in range(0, 32, 3):
+            for n in range(0, 32, 5):
+                for L in range(8):
+                    assert lev1[c, n, L] == lev[32 + c, 32 + n, L]
