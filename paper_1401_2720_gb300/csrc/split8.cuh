@@ -112,127 +112,40 @@ __device__ __forceinline__ int level_int(float v, int L) {
 }
 
 // The FP64 value 2^(e - 68) * T, T = sum_L lev[L] 256^(7-L), rounded once to
-// nearest (ties to even), in 64-bit integer arithmetic.  Level values are
-// exact integers, |lev| < 2^23, so T = hi 2^32 + lo with |hi|, |lo| < 2^48;
-// |T| is brought to the form M 2^32 + R (0 <= R < 2^32, M < 2^48), whose
-// leading 64 bits are rounded to 53.
-__device__ __forceinline__ double combine(const float (&lv)[kSlices], int e) {
-    long long v[kSlices];
-#pragma unroll
-    for (int L = 0; L < kSlices; ++L)
-        v[L] = (long long)level_int(lv[L], L);
-    const long long hi = v[0] * 16777216ll + v[1] * 65536ll + v[2] * 256ll + v[3];
-    const long long lo = v[4] * 16777216ll + v[5] * 65536ll + v[6] * 256ll + v[7];
-    // T = H 2^32 + L, 0 <= L < 2^32 (floor division of lo by 2^32)
-    const long long H = hi + (lo >> 32);
-    const uint32_t L = (uint32_t)(unsigned long long)lo;
-    const bool neg = H < 0;
-    unsigned long long M;
-    uint32_t R;
-    if (!neg) {
-        M = (unsigned long long)H;
-        R = L;
-    } else if (L != 0u) {            // -T = (-H - 1) 2^32 + (2^32 - L)
-        M = (unsigned long long)(-H - 1);
-        R = 0u - L;
-    } else {
-        M = (unsigned long long)(-H);
-        R = 0u;
-    }
-    unsigned long long mant;
-    int ex;                          // |T| = mant 2^(ex - 52), mant in [2^52, 2^53)
-    if (M == 0ull) {
-        if (R == 0u) return 0.0;
-        const int p = 31 - __clz((int)R);    // exact: at most 32 significant bits
-        mant = (unsigned long long)R << (52 - p);
-        ex = p;
-    } else {
-        const int s = __clzll((long long)M);  // 16 .. 63
-        unsigned long long top;              // leading one at bit 63
-        bool sticky;
-        if (s < 32) {
-            top = (M << s) | (unsigned long long)(R >> (32 - s));
-            sticky = (uint32_t)(R << s) != 0u;
-        } else {
-            top = (M << s) | ((unsigned long long)R << (s - 32));
-            sticky = false;
-        }
-        ex = 95 - s;
-        mant = top >> 11;
-        const uint32_t rem = (uint32_t)top & 0x7ffu;
-        if (rem > 0x400u || (rem == 0x400u && (sticky || (mant & 1ull)))) ++mant;
-        if (mant >> 53) {
-            mant >>= 1;
-            ++ex;
-        }
-    }
-    const int be = ex + e - 68 + 1023;
-    const unsigned long long sign = (unsigned long long)neg << 63;
-    if (be >= 1 && be <= 2046)
-        return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0x000fffffffffffffull)));
-    // rare: the result is outside the normal range; +-mant is exact
-    const double r = __longlong_as_double((long long)(sign | (1075ull << 52) | (mant & 0x000fffffffffffffull)));
-    return split::scale_slow(r, ex - 52 + e - 68);
-}
-
-// The same value as combine(), computed with 32-bit integer operations only
-// and without data-dependent branches (so that the compiler can interleave
-// the recombination of several outputs): the levels are carry-propagated
-// into bytes,
-//   T = D0 2^56 + F,  F = d1 d2 ... d7 (bytes, 0 <= F < 2^56),
-// |T| is shifted left by whole words and then bits until its leading one is
-// at bit 95 of a 96-bit value, and rounded once to 53 bits, ties to even.
-//
-// combine_levels takes the level values as ints (any |lev| < 2^30, e.g. the
-// Gram's sums of several accumulators); combine32 converts a length-64
-// contraction's FP32 levels first.
+// nearest (ties to even).  Level values are ints, |lev| < 2^30 (a length-64
+// contraction's FP32 levels through combine32, or the Gram's sums over
+// several chunks), so hi = sum_{L<4} lev[L] 256^(3-L) and lo = sum_{L>=4}
+// lev[L] 256^(7-L) are below 2^55 and T = H 2^32 + R0 with H = hi + floor(lo
+// / 2^32), 0 <= R0 < 2^32.  |T| = M 2^32 + R (M < 2^56) is shifted right by
+// k in {0, 8, 16, 24} bits, the least multiple of 8 that brings it below
+// 2^64: X = floor(|T| / 2^k) then has at least 57 significant bits when
+// k > 0, and the discarded bits are ORed into its last bit (rounding to
+// odd), so the correctly rounded conversion of X to FP64 (nearest, ties to
+// even) is |T| 2^-k rounded once to 53 bits -- at least 2 bits beyond the
+// 53 kept and a sticky last bit decide the rounding as the exact value
+// would.  The power of two 2^(k + e - 68) is added to the exponent field.
 __device__ __forceinline__ double combine_levels(const int (&l)[kSlices], int e) {
-    uint32_t d[kSlices];
-    int c = 0;
-#pragma unroll
-    for (int L = kSlices - 1; L >= 1; --L) {
-        const int x = l[L] + c;
-        d[L] = (uint32_t)x & 255u;
-        c = x >> 8;                      // arithmetic: floor division by 256
-    }
-    const int D0 = l[0] + c;             // |D0| < 2^31 for |lev| < 2^30
-    // F = (Fh << 32) | Fl, Fh = d1 d2 d3 (24 bits), Fl = d4 d5 d6 d7
-    const uint32_t Fl0 = __byte_perm(__byte_perm(d[7], d[6], 0x0040u), __byte_perm(d[5], d[4], 0x0040u), 0x5410u);
-    const uint32_t Fh0 = __byte_perm(__byte_perm(d[3], d[2], 0x0040u), d[1], 0x5410u);
-    // |T| = A 2^56 + Fh 2^32 + Fl; for T < 0 the 80-bit two's complement:
-    // (-D0) 2^56 - F = (-D0 - [F != 0]) 2^56 + (2^56 - F) mod 2^56
-    const bool neg = D0 < 0;
-    const bool zlo = Fl0 == 0u, zf = zlo && Fh0 == 0u;
-    const uint32_t Fl = neg ? 0u - Fl0 : Fl0;
-    const uint32_t Fh = neg ? ((0u - Fh0 - (zlo ? 0u : 1u)) & 0x00ffffffu) : Fh0;
-    const uint32_t A = neg ? (uint32_t)(-D0) - (zf ? 0u : 1u) : (uint32_t)D0;
-    // 96-bit view n2:n1:n0, then whole-word shifts while the top word is zero
-    uint32_t w2 = A >> 8, w1 = (A << 24) | Fh, w0 = Fl;
-    int ex = 95;                         // bit position of the leading one after the shifts
-    const bool s1 = w2 == 0u;
-    w2 = s1 ? w1 : w2; w1 = s1 ? w0 : w1; w0 = s1 ? 0u : w0; ex -= s1 ? 32 : 0;
-    const bool s2 = w2 == 0u;
-    w2 = s2 ? w1 : w2; w1 = s2 ? w0 : w1; w0 = s2 ? 0u : w0; ex -= s2 ? 32 : 0;
-    const bool zero = w2 == 0u;
-    const int z = __clz((int)w2);        // 32 if zero (then the result is 0 below)
-    const uint32_t hi = __funnelshift_l(w1, w2, z), lo = __funnelshift_l(w0, w1, z);
-    const bool sticky = (w0 << (z & 31)) != 0u && z < 32;
-    ex -= z;
-    // mantissa = top 53 bits of hi:lo; the next 11 bits and sticky round it
-    unsigned long long mant = ((unsigned long long)(hi >> 11) << 32) | __funnelshift_r(lo, hi, 11);
-    const uint32_t rem = lo & 0x7ffu;
-    const bool up = rem > 0x400u || (rem == 0x400u && (sticky || (mant & 1ull)));
-    mant += up ? 1ull : 0ull;
-    const bool carry = (mant >> 53) != 0ull;   // rounded up to 2^53
-    mant = carry ? (mant >> 1) : mant;
-    ex += carry ? 1 : 0;
-    const int be = ex + e - 68 + 1023;
-    const uint32_t sign = neg ? 0x80000000u : 0u;
-    const uint32_t mh = (uint32_t)(mant >> 32) & 0x000fffffu, ml = (uint32_t)mant;
-    if (zero) return 0.0;
-    if (be >= 1 && be <= 2046) return __hiloint2double((int)(sign | ((uint32_t)be << 20) | mh), (int)ml);
-    const double r = __hiloint2double((int)(sign | (1075u << 20) | mh), (int)ml);   // +-mant, exact
-    return split::scale_slow(r, ex - 52 + e - 68);
+    const long long hi = (long long)l[0] * 16777216ll + (long long)l[1] * 65536ll + (long long)l[2] * 256ll + l[3];
+    const long long lo = (long long)l[4] * 16777216ll + (long long)l[5] * 65536ll + (long long)l[6] * 256ll + l[7];
+    const long long H = hi + (lo >> 32);               // arithmetic: floor division by 2^32
+    const uint32_t R0 = (uint32_t)(unsigned long long)lo;
+    const bool neg = H < 0;
+    // |T| = M 2^32 + R: for T < 0, -T = (-H - 1) 2^32 + (2^32 - R0), or (-H) 2^32 if R0 = 0
+    const unsigned long long M =
+        neg ? (R0 != 0u ? (unsigned long long)(~H) : (unsigned long long)(-H)) : (unsigned long long)H;
+    const uint32_t R = neg ? 0u - R0 : R0;
+    const uint32_t Mh = (uint32_t)(M >> 32);           // < 2^24
+    const int k = (32 - __clz((int)Mh) + 7) & ~7;      // 0 if Mh = 0, else 8 ceil(bits(Mh) / 8)
+    unsigned long long X = (M << (32 - k)) | (unsigned long long)(R >> k);
+    X |= (R & ((1u << k) - 1u)) != 0u ? 1ull : 0ull;
+    const double d = __ull2double_rn(X);                // the one rounding
+    if (X == 0ull) return 0.0;
+    const int s = k + e - 68;
+    const int dh = __double2hiint(d);                   // d > 0: sign bit clear
+    const int be = (dh >> 20) + s;
+    const int sign = neg ? (int)0x80000000u : 0;
+    if (be >= 1 && be <= 2046) return __hiloint2double(sign | (dh + s * 1048576), __double2loint(d));
+    return split::scale_slow(neg ? -d : d, s);          // rare: outside the normal range
 }
 
 __device__ __forceinline__ double combine32(const float (&lv)[kSlices], int e) {

@@ -11,6 +11,8 @@ of the GPU code: the digit bias and ranges, that every level sum is an integer
 small enough for exact FP32 accumulation, and that the result is at least as
 accurate, column by column, as an FP64 dot product of the same length.
 """
+import math
+import random
 from fractions import Fraction
 
 import numpy as np
@@ -160,28 +162,6 @@ def _stacked_gram_levels(Dg: np.ndarray, BB: int):
     return acc, lev
 
 
-def _upper_half_gram_levels(Dg: np.ndarray):
-    """The tcgen05 Gram's half 1 for BB = 64 (outputs n >= 32, which need the
-    columns c >= 32 only): the A operand is the 4 slices 4 g .. 4 g + 3 of
-    those columns (lane 32 s + c - 32), the B operand slices 0 .. 7 - 4 g,
-    MMA g adds at column block 4 g, so lane 32 s + c', block j accumulates
-    sum_{4 g <= j} sum_k d_{4 g + s}(k, 32 + c') d_{j - 4 g}(k, n).  Returns
-    those sums [lane, block, n - 32] and the levels [c - 32, n - 32, L]."""
-    acc = np.zeros((128, 8, 32), dtype=object)
-    for g in range(2):
-        for s in range(4):
-            for j in range(4 * g, 8):
-                for c in range(32):
-                    acc[32 * s + c, j, :] += [int(Dg[4 * g + s, :, 32 + c] @ Dg[j - 4 * g, :, 32 + n])
-                                              for n in range(32)]
-    lev = np.zeros((32, 32, 8), dtype=object)
-    for L in range(8):
-        for s in range(4):
-            if L - s >= 0:
-                lev[:, :, L] += acc[32 * s:32 * (s + 1), L - s, :]
-    return acc, lev
-
-
 @pytest.mark.parametrize("BB", [16, 64])
 @pytest.mark.parametrize("kind", ["coherent", "extreme"])
 def test_stacked_gram_column_sums_exact_and_levels(BB, kind):
@@ -214,10 +194,55 @@ def test_stacked_gram_column_sums_exact_and_levels(BB, kind):
     # reach 2^14 per row, the other two hold d_0, |d_0| <= 64)
     assert max(abs(int(v)) for v in lev.flat) <= 7 * 2 ** 22
     assert 32 * max(abs(int(v)) for v in lev.flat) < 2 ** 30
-    if BB == 64:
-        acc1, lev1 = _upper_half_gram_levels(Dg)
-        assert max(abs(int(v)) for v in acc1.flat) <= 2 ** 23
-        for c in range(0, 32, 3):
-            for n in range(0, 32, 5):
-                for L in range(8):
-                    assert lev1[c, n, L] == lev[32 + c, 32 + n, L]
+
+
+def _combine_by_conversion(l, e):
+    """The steps of split8::combine_levels: T = H 2^32 + R0 from the two
+    half sums, |T| = M 2^32 + R, a right shift by k in {0, 8, 16, 24} to below
+    2^64 with the discarded bits ORed into the last bit, one correctly rounded
+    conversion to FP64 (Python's int -> float rounds to nearest, ties to even)
+    and an exact power-of-two scale."""
+    hi = l[0] * 2 ** 24 + l[1] * 2 ** 16 + l[2] * 2 ** 8 + l[3]
+    lo = l[4] * 2 ** 24 + l[5] * 2 ** 16 + l[6] * 2 ** 8 + l[7]
+    H, R0 = hi + (lo >> 32), lo & 0xFFFFFFFF
+    neg = H < 0
+    M = (~H if R0 else -H) if neg else H
+    R = (-R0) & 0xFFFFFFFF if neg else R0
+    assert 0 <= M < 2 ** 56
+    k = ((M >> 32).bit_length() + 7) & ~7
+    X = (M << (32 - k)) | (R >> k)
+    assert X < 2 ** 64 and (k == 0 or X >= 2 ** 56)
+    if R & ((1 << k) - 1):
+        X |= 1
+    r = math.ldexp(float(X), k + e - 68)
+    return -r if neg else r
+
+
+def test_combine_by_conversion_rounds_once():
+    """The level recombination (rounding to odd at >= 57 bits, then one
+    round-to-nearest conversion) equals T 2^(e-68) rounded once, ties to even:
+    random levels up to the 2^30 bound, sparse levels, and constructed exact
+    ties and near-ties of every magnitude up to 2^86, both signs."""
+    rng = random.Random(7)
+
+    def exact(l, e):
+        T = sum(l[L] * 256 ** (7 - L) for L in range(8))
+        return float(Fraction(T) * Fraction(2) ** (e - 68)) if T else 0.0
+
+    cases = []
+    for it in range(4000):
+        bound = [2 ** 23, 2 ** 30 - 1, 300][it % 3]
+        cases.append([rng.randint(-bound, bound) for _ in range(8)])
+    for it in range(4000):
+        bits = rng.randint(54, 86)
+        s = bits - 53
+        T = ((rng.getrandbits(52) | 2 ** 52) << s) + rng.choice([2 ** (s - 1), 2 ** (s - 1) - 1, 2 ** (s - 1) + 1])
+        T = -T if it % 2 else T
+        l = [0] * 8
+        for L in range(7, 0, -1):
+            l[L], T = T & 255, T >> 8
+        l[0] = T
+        cases.append(l)
+    for l in cases:
+        e = rng.randint(-150, 150)
+        assert _combine_by_conversion(l, e) == exact(l, e), (l, e)
