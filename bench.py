@@ -53,9 +53,9 @@ SPLIT_UPDATE_BYTES_PER_PAIR_ROW = 488.461e6 / (2 * 64 * 4096)
 SPLIT_PRODUCTS = 45
 TC_PRODUCTS = 36
 # dram__bytes_read.sum + dram__bytes_write.sum of one update_tc<64> launch (ncu,
-# 4096x4096 graded, b = 32, first sweep: every pair updated; 283.18 MB read +
-# 208.69 MB written) divided by its 64 pairs x 8192 (G and V) rows
-TC_UPDATE_BYTES_PER_PAIR_ROW = 491.868e6 / (64 * 8192)
+# 4096x4096 graded, b = 32, first sweep: every pair updated; 283.55 MB read +
+# 207.89 MB written) divided by its 64 pairs x 8192 (G and V) rows
+TC_UPDATE_BYTES_PER_PAIR_ROW = 491.436e6 / (64 * 8192)
 
 WORKLOADS = {
     # name: (m, n, generator, description)

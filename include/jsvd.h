@@ -60,10 +60,9 @@ extern "C" {
  * power-of-two scaled fixed-point operands (exact FP32 accumulation of the
  * digit products, one FP64 rounding per result); with the column scaling they
  * apply, their error is at or below that of the FP64 FMA form.
- *   SPLIT:       Gram from 9 7-bit slices (45 products, mma.sync); update on
- *                tcgen05 with tensor-memory accumulators from 8 8-bit slices
- *                (36 products) -- the default.
- *   SPLIT_SYNC:  both from 9 7-bit slices on mma.sync.
+ *   SPLIT:       Gram and update on tcgen05 with tensor-memory accumulators,
+ *                both from 8 8-bit slices (36 products) -- the default.
+ *   SPLIT_SYNC:  both from 9 7-bit slices (45 products) on mma.sync.
  * Used by jsvd_dgesvj, jsvd_dhsvj and the FP64 stage of the mixed solver; the
  * batched solver runs the mma.sync forms for both split modes. */
 #define JSVD_CONTRACT_FP64        0  /* FP64 FMA kernels */
