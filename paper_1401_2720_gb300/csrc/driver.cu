@@ -600,7 +600,7 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
     // where the two were within 2 %).  The FP64 FMA form overlaps the V update
     // on the side stream.
     const bool split = o.contraction == JSVD_CONTRACT_SPLIT || o.contraction == JSVD_CONTRACT_SPLIT_SYNC;
-    // the tcgen05 update (8-bit digit images) or the mma.sync one (7-bit)
+    // the tcgen05 Gram and update (8-bit digit images) or the mma.sync ones (7-bit)
     const bool tc = o.contraction == JSVD_CONTRACT_SPLIT;
     const size_t bsl_pairs = (size_t)npairs * 2 * (size_t)split_b_elems_rt(BB);
     if (split) {
@@ -822,9 +822,9 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
         // The FP32 stage is a preconditioner: it ends once a sweep makes
         // fewer than 30 % as many proper rotations as its first one.  Its later
         // sweeps only polish what the FP64 sweeps redo at FP64 accuracy, and an
-        // FP32 sweep costs ~2/3 of a tensor-core FP64 one (8192 x 4096, sigma
-        // in [1e-12, 1]: thresholds 0.01 / 0.15 / 0.3 / 0.6 gave 18+22 /
-        // 17+21 / 14+21 / 7+26 FP32+FP64 sweeps, 5.24 / 5.06 / 4.80 / 5.07 s)
+        // FP32 sweep costs ~3/4 of a tensor-core FP64 one (8192 x 4096, sigma
+        // in [1e-12, 1]: thresholds 0.05 / 0.15 / 0.3 / 0.6 gave 18+21 /
+        // 17+21 / 14+21 / 7+27 FP32+FP64 sweeps, 5.12 / 5.03 / 4.73 / 4.94 s)
         if ((rc = sweep_loop(o.max_sweeps, &low_done, &low_conv, 0.3))) return rc;
         inf.sweeps_low = low_done;
         // Stage 2: Q = polar factor of V32 in FP64, G := G Q, V := Q.

@@ -13,9 +13,11 @@
 //                      one row chunk per CTA (Eq. (2.9) / Alg. 4.2).
 //
 // BB = 2b is the order of the pivot block.  With PStepArgs::split (the
-// default for the FP64 sweeps) the Gram and update launches are the
-// tensor-core kernels gram_split / update_split (sweep_split.cu,
-// split_kernels.cuh), and pair_jacobi also writes the split right factors.
+// default for the FP64 sweeps) the Gram and update launches are tensor-core
+// kernels -- with PStepArgs::tc (the default) gram_tc / update_tc on tcgen05
+// (gram_tc.cu, update_tc.cu), else gram_split / update_split on mma.sync
+// (sweep_split.cu, split_kernels.cuh) -- and pair_jacobi also writes the
+// split right factors.
 // In the FP64 FMA form all arithmetic is FP64 and the FP64 pipe is the bound,
 // so every FMA that is issued does useful work: the Gram kernel computes only
 // the lower triangle, the update skips pairs whose V' is the identity.  In the
@@ -61,8 +63,8 @@ struct PStepArgs {
     int *bexp;              // [npairs][2][BB] column exponent bounds of the right factors
     int *dexp;              // [npairs][BB] column scales of [G_P G_Q]
     int *gexp;              // [n_pad] exponent bound of every column of G: |g_ij| < 2^gexp[j]
-    int tc;                 // 1: the update runs on tcgen05 (update_tc.cu); bslice then holds the
-                            // 8-bit images [npairs][2][split8::image_elems<BB>]
+    int tc;                 // 1: the Gram and the update run on tcgen05 (gram_tc.cu, update_tc.cu);
+                            // bslice then holds the 8-bit images [npairs][2][split8::image_elems<BB>]
 };
 
 
