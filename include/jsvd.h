@@ -214,6 +214,26 @@ int jsvd_dgesvj_noalloc(int m, int n, const double *A, int lda, double *S, doubl
  * Host only; needs no GPU.                                                  */
 int jsvd_pivot_table(int strategy, int nblocks, int *out_pairs);
 
+/* One block p-step of the FP64 block-oriented method (Sec. 2 and Sec. 4: for
+ * every pivot pair (P, Q) of row `step` of the block p-strategy table of
+ * order n/b for `strategy`, the Gram matrix (2.7), its Cholesky factor
+ * R = L^T (Sec. 4.1), one inner sweep of the pointwise method on R with the
+ * same strategy at order 2b (Sec. 4.3, Eqs. (4.3)-(4.6)), and the update
+ * (2.9) of G and V), with the kernels and the launch configuration of one
+ * p-step of jsvd_dgesvj.  G (device, m x n, column-major, ld ldg) and V
+ * (device, n x n, ld ldv; NULL: G only) are read and overwritten in place.
+ * b in {8, 16, 32}; n a multiple of 2b with n/b an order the strategy admits
+ * (no bordering: jsvd_pivot_table accepts it); 0 <= step < n/b - 1;
+ * contraction = JSVD_CONTRACT_*.  No initial scaling is applied, so the
+ * squared column norms must stay inside the FP64 range.  info (host, may be
+ * NULL) receives the step's rotation, proper-rotation, updated-pair and
+ * breakdown counts and the normalised off-diagonal maximum (sweeps = 0).
+ * Synchronises the context stream.  Returns 0, a negative argument index, or
+ * JSVD_ERR_NONFINITE / JSVD_ERR_UNSUPPORTED / JSVD_ERR_ALLOC / JSVD_ERR_CUDA /
+ * JSVD_ERR_TIMEOUT.                                                          */
+int jsvd_block_pstep(jsvd_ctx_t ctx, int m, int n, int b, int strategy, int step, double *G, int ldg,
+                     double *V, int ldv, int contraction, jsvd_info *info);
+
 /* Sums of squares of the columns of A (device, m x n, ld lda) by DRDSSQ
  * (App. A), the parallel scaled sum the solvers use for the column norms of
  * the kernel Sigma and for their initial scaling: ||a_j||^2 = f[j] 2^e[j]

@@ -865,6 +865,117 @@ int jsvd_ctx::solve_on_stream(int m, int n, int nplus_in, const double *A, int l
     return converged ? JSVD_SUCCESS : JSVD_NOT_CONVERGED;
 }
 
+// One block p-step of the FP64 method on the caller's G and V, with the
+// kernels and launch configuration of a p-step of the solve: G and V are
+// copied into the row-padded workspaces, the step's Gram, Jacobi and update
+// kernels run, and the results are copied back.
+int jsvd_ctx::block_pstep(int m, int n, int b, int strategy, int step, double *Gc, int ldg, double *Vc, int ldv,
+                          int contraction, jsvd_info *info) {
+    if (b != 8 && b != 16 && b != 32) {
+        last_error = "block width must be 8, 16 or 32";
+        return JSVD_ERR_UNSUPPORTED;
+    }
+    if (strategy < 0 || strategy > 4) return JSVD_ERR_UNSUPPORTED;
+    if (contraction != JSVD_CONTRACT_FP64 && contraction != JSVD_CONTRACT_SPLIT &&
+        contraction != JSVD_CONTRACT_SPLIT_SYNC) {
+        last_error = "unknown contraction mode";
+        return JSVD_ERR_UNSUPPORTED;
+    }
+    const int BB = 2 * b, nb = n / b, npairs = nb / 2;
+    if (n % BB != 0 || admissible_order(strategy, nb) != nb) {
+        last_error = "n must be a multiple of 2b with n/b an order the strategy admits";
+        return JSVD_ERR_UNSUPPORTED;
+    }
+    if (step < 0 || step >= nb - 1) return -6;
+    const int g_rows = (int)round_up(m, kRowAlign), v_rows = (int)round_up(n, kRowAlign);
+    const int g_chunks = g_rows / kGramRows;
+    const bool split = contraction != JSVD_CONTRACT_FP64, tc = contraction == JSVD_CONTRACT_SPLIT;
+    int rc;
+    if ((rc = ensure(g, sizeof(double) * (size_t)g_rows * n))) return rc;
+    if (Vc && (rc = ensure(v, sizeof(double) * (size_t)v_rows * n))) return rc;
+    if ((rc = ensure(part, sizeof(double) * (size_t)npairs * g_chunks * (BB * (BB + 1) / 2)))) return rc;
+    if ((rc = ensure(vprime, sizeof(double) * (size_t)npairs * BB * BB))) return rc;
+    if ((rc = ensure(vflag, sizeof(int) * (size_t)npairs))) return rc;
+    if ((rc = ensure(counters, sizeof(unsigned long long) * kCntSize))) return rc;
+    if (split) {
+        if ((rc = ensure(bslice, sizeof(uint16_t) * (size_t)npairs * 2 * split_b_elems_rt(BB)))) return rc;
+        if ((rc = ensure(bexp, sizeof(int) * (size_t)npairs * 2 * BB))) return rc;
+        if ((rc = ensure(dexp, sizeof(int) * (size_t)npairs * BB))) return rc;
+        if ((rc = ensure(gexp, sizeof(int) * (size_t)n))) return rc;
+    }
+    if (!host_counters) {
+        if (cudaMallocHost(&host_counters, sizeof(unsigned long long) * kCntSize) != cudaSuccess) {
+            cudaGetLastError();
+            return JSVD_ERR_ALLOC;
+        }
+    }
+    const int *dtab = nullptr;
+    const unsigned char *dinner = nullptr;
+    if ((rc = table(strategy, nb, &dtab))) return rc;
+    if ((rc = inner_table(strategy, BB, &dinner))) return rc;
+    double *G = (double *)g.ptr, *V = Vc ? (double *)v.ptr : nullptr;
+    unsigned long long *cnt = (unsigned long long *)counters.ptr;
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kCntSize, stream);
+    // the copies in (zero rows below m and n; no bordering)
+    k_init_g<<<1024, 256, 0, stream>>>(Gc, ldg, m, n, n, 0, G, g_rows, g_rows, n, cnt + kCntErr);
+    if (V) k_init_g<<<1024, 256, 0, stream>>>(Vc, ldv, n, n, n, 0, V, v_rows, v_rows, n, cnt + kCntErr);
+
+    PStepArgs a{};
+    a.G = G; a.ldg = g_rows; a.g_rows = g_rows;
+    a.V = V; a.ldv = v_rows; a.v_rows = v_rows;
+    a.table = dtab; a.npairs = npairs; a.step = step; a.inner = dinner;
+    a.b = b; a.nplus = n; a.bord_lo = n; a.bord_hi = n; a.inner_sweeps = 1;
+    a.fp32 = 0; a.eps = kEps;
+    a.part = (double *)part.ptr; a.vprime = (double *)vprime.ptr; a.vflag = (int *)vflag.ptr;
+    a.counters = cnt;
+    a.split = split ? 1 : 0; a.tc = tc ? 1 : 0;
+    if (split) {
+        a.bslice = (uint16_t *)bslice.ptr; a.bexp = (int *)bexp.ptr; a.dexp = (int *)dexp.ptr;
+        a.gexp = (int *)gexp.ptr;
+        a.g_chunks = g_rows / kGramRowsSplit;
+        a.g_parts = tc ? gram_tc_parts(a) : a.g_chunks;
+        launch_col_maxexp(G, g_rows, g_rows, n, a.gexp, stream);
+    } else {
+        a.g_chunks = g_chunks;
+        a.g_parts = g_chunks;
+    }
+    launch_phase(BB, Phase::Gram, a, stream);
+    launch_phase(BB, Phase::Jacobi, a, stream);
+    launch_phase(BB, Phase::UpdateGV, a, stream);
+    prof_launches[4] += (V ? 2 : 1) + (split ? 1 : 0);
+    prof_launches[0] += 1; prof_launches[1] += 1; prof_launches[2] += 1;
+    if ((rc = check("p-step"))) return rc;
+    cudaMemcpy2DAsync(Gc, sizeof(double) * (size_t)ldg, G, sizeof(double) * (size_t)g_rows, sizeof(double) * m, n,
+                      cudaMemcpyDeviceToDevice, stream);
+    if (V)
+        cudaMemcpy2DAsync(Vc, sizeof(double) * (size_t)ldv, V, sizeof(double) * (size_t)v_rows, sizeof(double) * n,
+                          n, cudaMemcpyDeviceToDevice, stream);
+    cudaMemcpyAsync(host_counters, cnt, sizeof(unsigned long long) * kCntSize, cudaMemcpyDeviceToHost, stream);
+    if ((rc = sync("p-step"))) return rc;
+    if (host_counters[kCntErr] & 1ull) {
+        last_error = "input holds Inf or NaN";
+        return JSVD_ERR_NONFINITE;
+    }
+    if (host_counters[kCntErr] & 4ull) {
+        last_error = "a bounded wait of a tensor-core kernel gave up";
+        return JSVD_ERR_TIMEOUT;
+    }
+    if (info) {
+        jsvd_info f{};
+        f.b = b;
+        f.rotations = (long long)host_counters[kCntRot];
+        f.proper_rotations = (long long)host_counters[kCntProper];
+        f.pairs_updated = (long long)host_counters[kCntUpdated];
+        f.breakdowns = (long long)host_counters[kCntBreak];
+        double off;
+        const unsigned long long bits = host_counters[kCntOff];
+        memcpy(&off, &bits, sizeof off);
+        f.off_norm = off;
+        *info = f;
+    }
+    return 0;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 
@@ -983,6 +1094,18 @@ int jsvd_dhsvj(jsvd_ctx_t ctx, int m, int n, int n_plus, const double *G, int ld
     if (V && ldv < n) return -11;
     cudaSetDevice(ctx->device);
     return ctx->solve(m, n, n_plus, G, ldg, S, U, ldu, V, ldv, opts, info, n_plus < n);
+}
+
+int jsvd_block_pstep(jsvd_ctx_t ctx, int m, int n, int b, int strategy, int step, double *G, int ldg, double *V,
+                     int ldv, int contraction, jsvd_info *info) {
+    if (!ctx) return -1;
+    if (m < 1) return -2;
+    if (n < 2) return -3;
+    if (!G) return -7;
+    if (ldg < m) return -8;
+    if (V && ldv < n) return -10;
+    cudaSetDevice(ctx->device);
+    return ctx->block_pstep(m, n, b, strategy, step, G, ldg, V, ldv, contraction, info);
 }
 
 int jsvd_column_sumsq(jsvd_ctx_t ctx, int m, int n, const double *A, int lda, int *e, double *f) {

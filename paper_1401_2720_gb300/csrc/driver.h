@@ -81,4 +81,6 @@ struct jsvd_ctx {
                         double *V, int ldv, const jsvd_opts *opts, jsvd_info *info, bool hyperbolic);
     int solve(int m, int n, int nplus, const double *A, int lda, double *S, double *U, int ldu,
               double *V, int ldv, const jsvd_opts *opts, jsvd_info *info, bool hyperbolic);
+    int block_pstep(int m, int n, int b, int strategy, int step, double *G, int ldg, double *V, int ldv,
+                    int contraction, jsvd_info *info);
 };

@@ -61,7 +61,8 @@ EXPORTED = ["jsvd_default_opts", "jsvd_create", "jsvd_destroy", "jsvd_set_stream
             "jsvd_last_error", "jsvd_status_string", "jsvd_dgesvj", "jsvd_dhsvj",
             "jsvd_pivot_table", "jsvd_rotation_params", "jsvd_profile", "jsvd_profile_read",
             "jsvd_fp64_peak", "jsvd_bf16_mma_peak", "jsvd_dgesvj_batched", "jsvd_dgesvj_backward",
-            "jsvd_dgesvj_noalloc", "jsvd_sorted_pivot_table", "jsvd_column_sumsq", "jsvd_relative_test"]
+            "jsvd_dgesvj_noalloc", "jsvd_sorted_pivot_table", "jsvd_column_sumsq", "jsvd_relative_test",
+            "jsvd_block_pstep"]
 
 
 def library():
@@ -98,6 +99,7 @@ def library():
                                                 ctypes.POINTER(Info), P]
             lib.jsvd_sorted_pivot_table.argtypes = [P, I, I, P, P, P]
             lib.jsvd_column_sumsq.argtypes = [P, I, I, P, I, P, P]
+            lib.jsvd_block_pstep.argtypes = [P, I, I, I, I, I, P, I, P, I, I, ctypes.POINTER(Info)]
             _lib = lib
     return _lib
 
@@ -196,6 +198,25 @@ def hsvd(G: torch.Tensor, n_plus: int, *, with_v: bool = True, return_info: bool
         _raise(rc, h)
     res = (U, S, V)
     return (res + (dict(info.as_dict(), status=rc),)) if return_info else res
+
+
+def block_pstep(G: torch.Tensor, V: torch.Tensor | None, b: int, step: int, strategy: str = "rR",
+                contraction: str = "split") -> dict:
+    """One block p-step (Sec. 2, 4) of the FP64 method on G (m x n) and V
+    (n x n or None), in place, with the solver's kernels.  Both must be
+    column-major float64 CUDA tensors (e.g. X.t().contiguous().t())."""
+    m, n = G.shape
+    for X in (G, V):
+        if X is not None and (X.dtype != torch.float64 or not X.is_cuda or X.stride(0) != 1):
+            raise ValueError("block_pstep needs column-major float64 CUDA tensors")
+    info = Info()
+    h = context(G.device.index)
+    rc = library().jsvd_block_pstep(h, m, n, b, STRATEGIES[strategy], step, G.data_ptr(), G.stride(1),
+                                    V.data_ptr() if V is not None else None, V.stride(1) if V is not None else 1,
+                                    CONTRACTIONS[contraction], ctypes.byref(info))
+    if rc:
+        _raise(rc, h)
+    return info.as_dict()
 
 
 def pivot_table(strategy: str, nblocks: int) -> np.ndarray:

@@ -1,7 +1,8 @@
 """Parity of the block method's edge cases against the oracle's block method
 (Sec. 2, Sec. 4): rank-deficient pivot pairs (Cholesky breakdown, Sec. 4.1,
-read as "zero the pivot's column of L and count it") and the full row count
-of the benchmark's columns.
+read as "zero the pivot's column of L and count it"), the full row count
+of the benchmark's columns, and the benchmark's own 8192 x 8192 input and
+launch configuration, one block p-step at a time.
 
 Gates, per column j of G = U S (oracle column g_j):
   max_i |G_ij - G^o_ij| <= 1e-12 ||g_j||; an exactly zero oracle column must be
@@ -16,8 +17,11 @@ The breakdown decision is exact on both sides only where the Gram matrix is:
     compared element-wise after its first sweep of one pivot pair only, and on
     the converged singular values.
 """
+import os
+
 import numpy as np
 import pytest
+import torch
 
 import oracle as O
 from paper_1401_2720_gb300 import inputs as I
@@ -100,3 +104,57 @@ def test_full_column_length_elementwise(cuda, sweeps, contraction):
     G = _np(U) * _np(S)[None, :]
     assert_columns_close(G, r["G"])
     assert np.max(np.abs(_np(V) - r["V"])) <= 1e-12
+
+
+_BENCH = {}
+
+
+def _bench_oracle():
+    """The oracle's first two block p-steps on the 8192 x 8192 graded
+    benchmark input (seed 0), b = 32, reversed row-cyclic strategy, and its
+    disagreement with itself when the rows are reversed (the same exact
+    values, another summation order in every Gram entry and update): per step
+    (G, V, stats, floor of G per column relative to ||g_j||, floor of V)."""
+    if not _BENCH:
+        n, b = 8192, 32
+        A = I.graded_gaussian(n, n, seed=0)
+        tab = O.strategy_array("rR", n // b)
+        inner = O.strategy_array("rR", 2 * b)
+        O.set_threads(os.cpu_count() or 1)      # disjoint pairs: bitwise the same as one thread
+        try:
+            Go, Vo = np.array(A, order="F", copy=True), np.asfortranarray(np.eye(n))   # A stays the input
+            Gr, Vr = np.asfortranarray(A[::-1]), np.asfortranarray(np.eye(n))
+            for step in (0, 1):
+                Go, Vo, r = O.block_pstep(Go, Vo, b, tab[step], inner, inplace=True)
+                Gr, Vr, _ = O.block_pstep(Gr, Vr, b, tab[step], inner, inplace=True)
+                fg = (np.abs(Go - Gr[::-1]).max(axis=0) / np.linalg.norm(Go, axis=0)).max()
+                _BENCH[step] = (Go.copy(order="F"), Vo.copy(order="F"), r, fg, np.abs(Vo - Vr).max())
+        finally:
+            O.set_threads(1)
+        _BENCH["A"] = A
+    return _BENCH
+
+
+@pytest.mark.parametrize("contraction", ["split", "fp64"])
+def test_benchmark_input_psteps_elementwise(cuda, contraction):
+    """The benchmark's 8192 x 8192 input, b = 32, reversed row-cyclic strategy:
+    its first two block p-steps (128 pivot pairs each, every pair updated)
+    with the kernels and launch configuration of the benchmark's solve,
+    against the oracle's block p-steps, every entry of G and V.  Gates: G per
+    column max(1e-12, 10 floor_G) ||g_j||, V element-wise max(1e-12, 10
+    floor_V), where the floors are the oracle's own disagreement under row
+    reversal (measured: V 2.3e-12 and 1.7e-12 -- rotation angles of pairs whose
+    column norms nearly agree are that sensitive to the Gram's rounding)."""
+    ref = _bench_oracle()
+    n, b = 8192, 32
+    G = torch.from_numpy(np.ascontiguousarray(ref["A"].T)).to(cuda).t()
+    V = torch.eye(n, dtype=torch.float64, device=cuda).t()     # column-major view
+    for step in (0, 1):
+        Go, Vo, r, fg, fv = ref[step]
+        info = J.block_pstep(G, V, b, step, "rR", contraction)
+        assert info["pairs_updated"] == r["updated"] == n // (2 * b)
+        assert info["breakdowns"] == r["breakdowns"] == 0
+        worst = (np.abs(_np(G) - Go).max(axis=0) / np.linalg.norm(Go, axis=0)).max()
+        assert worst <= max(1e-12, 10 * fg), (step, worst, fg)
+        dv = np.abs(_np(V) - Vo).max()
+        assert dv <= max(1e-12, 10 * fv), (step, dv, fv)
