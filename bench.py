@@ -669,7 +669,7 @@ def main():
     p.add_argument("--max-sweeps", type=int, default=30)
     p.add_argument("--contraction", default="split", choices=["fp64", "split", "split_sync"],
                    help="FP64 block contractions: FP64 FMA kernels, or split bf16 digits on the tensor cores "
-                        "(split: tcgen05 update; split_sync: mma.sync update)")
+                        "(split: tcgen05 Gram and update; split_sync: mma.sync Gram and update)")
     p.add_argument("--inner-sweeps", type=int, default=1,
                    help="inner sweeps per pivot pair: 1 = block-oriented, 30 = full block (Sec. 4.3)")
     p.add_argument("--seed", type=int, default=0)
