@@ -37,8 +37,11 @@ import numpy as np
 from . import pivots
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "jacobi_oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+# JO_ORACLE_SRC / JO_ORACLE_BUILD: a hook for the mutation tests, which build a
+# copy of the C file with one planted mistake into a directory of their own
+# and check that the pins catch it; unset, the oracle is this directory's C.
+_SRC = os.environ.get("JO_ORACLE_SRC") or os.path.join(_HERE, "jacobi_oracle.c")
+_BUILD = os.environ.get("JO_ORACLE_BUILD") or os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libjacobi_oracle.so")
 _SO_Q = os.path.join(_BUILD, "libjacobi_oracle_q.so")
 _lock = threading.Lock()

@@ -1,0 +1,105 @@
+"""The oracle's pins are sensitive: each case plants one plausible mistake in a
+copy of the oracle's C file -- a wrong sign, a dropped factor or term, a
+transposed operand, a wrong index, a skipped step -- builds that copy into a
+directory of its own (JO_ORACLE_SRC / JO_ORACLE_BUILD) and runs the oracle's
+pin tests against it in a subprocess.  Every planted mistake must make at
+least one pin fail, and the unmodified copy must pass them all.  CPU only; the
+planted mistakes live only in temporary copies.
+
+Cases, by the passage each one breaks:
+  Eqs. (4.3)-(4.6)  the rotation: signs of h, ct2 and tan, the factor 2, the
+                    cs_2 form of the hyperbolic cosh, the small-angle shortcut;
+  Eqs. (4.1)/(4.2)  its application: the FMA signs, the multiply by cs;
+  Sec. 4.3          the relative test (|h_pq|), the P2 sort's direction in
+                    either J block, V's rotation and swap;
+  Eq. (2.7), 4.1    the Gram entry's operands, the Cholesky update and pivot;
+  Eq. (2.9)         the update's right factor transposed;
+  Sec. 4 (Sigma)    the column norm's square root;
+  App. A            DRDSSQ's large-entry scale and its even exponent;
+  Eq. (2.1)         the QR preprocessing's reflector;
+  the SVD adjoint   the sign of F, the V term, the projector term.
+Not a case: the sign of tan*h_pq in the P2 sort's new diagonal (reading R1).
+The annihilating rotation (|phi| <= pi/4) never reverses the order of h_pp and
+h_qq, and both new diagonal entries move by the same tan*h_pq, so comparing the
+old entries, or entries shifted either way, takes the same decision up to
+rounding ties: no outcome can tell the two signs apart (the 2x2 closed-form
+pin checks that formula of the new diagonal against the rotated matrix).
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+from tests.conftest import ROOT
+
+SRC = os.path.join(ROOT, "oracle", "jacobi_oracle.c")
+PINS = ["tests/test_oracle_rotation.py", "tests/test_oracle_svd.py", "tests/test_oracle_adjoint.py",
+        "tests/test_oracle_drdssq.py", "tests/test_oracle_quad.py"]
+
+# name: (exact text in the oracle's C file, the planted mistake)
+MUTATIONS = {
+    "h sign (4.3)": ("real h = hqq - tt * hpp;", "real h = hqq + tt * hpp;"),
+    "ct2 sign (4.3)": ("real ct2 = tt * (h / (2.0 * hpq));", "real ct2 = -tt * (h / (2.0 * hpq));"),
+    "factor 2 dropped (4.3)": ("real ct2 = tt * (h / (2.0 * hpq));", "real ct2 = tt * (h / hpq);"),
+    "small-angle shortcut bound (4.4)": ("else if (t > 0 && act2 < R_SQRT(JO_EPS))",
+                                         "else if (t > 0 && act2 < 1.0)"),
+    "tan sign (4.5)": ("real tnv = R_COPYSIGN(1.0 / act, ct2);", "real tnv = R_COPYSIGN(1.0 / act, -ct2);"),
+    "cs_2 with t = +1 for cosh (4.6)": ("csv = act / R_SQRT(R_FMA(act, act, tt));",
+                                       "csv = act / R_SQRT(R_FMA(act, act, 1.0));"),
+    "trigonometric FMA sign (4.1)": ("xn = R_FMA(-tn, yi, xi);", "xn = R_FMA(tn, yi, xi);"),
+    "hyperbolic FMA sign (4.2)": ("xn = R_FMA(tn, yi, xi);", "xn = R_FMA(-tn, yi, xi);"),
+    "cs multiply dropped on one column": ("if (cs != 1.0) { xn = cs * xn; yn = cs * yn; }",
+                                          "if (cs != 1.0) { xn = cs * xn; }"),
+    "relative test without |h_pq|": ("R_FABS(hpq) < c_eps", "hpq < c_eps"),
+    "P2 sort direction, J+ block": ("if (l < nplus && npp < nqq) swap = 1;", "if (l < nplus && npp > nqq) swap = 1;"),
+    "P2 sort direction, J- block": ("if (k >= nplus && npp > nqq) swap = 1;", "if (k >= nplus && npp < nqq) swap = 1;"),
+    "V not rotated": ("if (nv) apply_rot(nv, vp, vq, t, cs, tn);", "if (0) apply_rot(nv, vp, vq, t, cs, tn);"),
+    "V not swapped": ("if (nv) swap_cols(nv, vp, vq);", "if (0) swap_cols(nv, vp, vq);"),
+    "Gram operand index (2.7)": ("H[i + j * bb] = dot(m, X + (size_t)i * m, X + (size_t)j * m);",
+                                 "H[i + j * bb] = dot(m, X + (size_t)i * m, X + (size_t)i * m);"),
+    "Cholesky update sign (4.1)": ("d = R_FMA(-L[k + j * bb], L[k + j * bb], d);",
+                                   "d = R_FMA(L[k + j * bb], L[k + j * bb], d);"),
+    "Cholesky division dropped (4.1)": ("L[i + k * bb] = s / lkk;", "L[i + k * bb] = s;"),
+    "update with V' transposed (2.9)": ("s = R_FMA(X[i + (size_t)k * rows], W[k + j * bb], s);",
+                                        "s = R_FMA(X[i + (size_t)k * rows], W[j + k * bb], s);"),
+    "column norm without the root": ("sigma[j] = R_SQRT(dot(m, G + (size_t)j * ldg, G + (size_t)j * ldg));",
+                                     "sigma[j] = dot(m, G + (size_t)j * ldg, G + (size_t)j * ldg);"),
+    "DRDSSQ large-entry scale sign": ("if (b > nu_h) { double y = ldexp(a, l2);",
+                                      "if (b > nu_h) { double y = ldexp(a, -l2);"),
+    "DRDSSQ odd exponent": ("int mp = -(((m % 2) + 2) % 2);", "int mp = 0;"),
+    "QR reflector sign (2.1)": ("c[r] = R_FMA(-f, x[r], c[r]);", "c[r] = R_FMA(f, x[r], c[r]);"),
+    "adjoint F sign": ("real F = 1.0 / (s[j] * s[j] - s[i] * s[i]);", "real F = 1.0 / (s[i] * s[i] - s[j] * s[j]);"),
+    "adjoint V term dropped": ("v = F * a * s[j] + s[i] * (F * c);", "v = F * a * s[j];"),
+    "adjoint projector term dropped": ("Z[r + (size_t)j * m] = (dU[r + (size_t)j * m] - a) / s[j];",
+                                       "Z[r + (size_t)j * m] = dU[r + (size_t)j * m] / s[j];"),
+}
+
+
+def _run_pins(text: str):
+    d = tempfile.mkdtemp(prefix="jo_mutant_")
+    try:
+        src = os.path.join(d, "jacobi_oracle.c")
+        with open(src, "w") as f:
+            f.write(text)
+        env = dict(os.environ, JO_ORACLE_SRC=src, JO_ORACLE_BUILD=os.path.join(d, "_build"))
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+        return r.returncode, r.stdout[-2500:] + r.stderr[-1000:]
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+
+
+def test_pins_catch_every_planted_mistake():
+    base = open(SRC).read()
+    cases = {"unmodified copy": base}
+    for name, (old, new) in MUTATIONS.items():
+        assert base.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+        cases[name] = base.replace(old, new)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        results = dict(zip(cases, ex.map(_run_pins, cases.values())))
+    rc, out = results.pop("unmodified copy")
+    assert rc == 0, out
+    survivors = [name for name, (code, _) in results.items() if code == 0]
+    assert not survivors, f"planted mistakes no pin catches: {survivors}"

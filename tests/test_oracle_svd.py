@@ -51,6 +51,26 @@ def test_matches_mpmath_high_precision():
     assert np.max(np.abs(S - s_ref) / s_ref) <= 1e-13
 
 
+@pytest.mark.parametrize("nplus", [2, 0])
+def test_p2_sort_after_one_rotation(nplus):
+    """Sec. 4.3 subphase 5 (reading R1 for the sign of the new diagonal): after
+    the rotation of a trigonometric pair its columns are ordered by their new
+    norms -- non-increasing in the J+ block, non-decreasing in the J- block --
+    so one step on a two-column matrix leaves them in that order."""
+    rng = np.random.default_rng(12)
+    swaps = 0
+    for _ in range(200):
+        A = np.asfortranarray(rng.standard_normal((6, 2)) * 10.0 ** rng.uniform(-1, 1, size=2))
+        r = O.hestenes(A, nplus=nplus, max_sweeps=1)
+        h0, h1 = np.sum(r["G"] ** 2, axis=0)
+        if nplus == 2:
+            assert h0 >= h1 * (1 - 1e-12)
+        else:
+            assert h0 <= h1 * (1 + 1e-12)
+        swaps += r["swaps"]
+    assert 0 < swaps < 200                        # both orders occur before the sort
+
+
 def test_tiny_bruteforce_2x2():
     A = np.asfortranarray(np.array([[3.0, 1.0], [1.0, 2.0]]))
     U, S, V, _ = O.svd(A)
