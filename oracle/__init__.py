@@ -34,7 +34,17 @@ import threading
 
 import numpy as np
 
-from . import pivots
+if os.environ.get("JO_PIVOTS_SRC"):
+    # the mutation tests' hook for a planted-mistake copy of pivots.py
+    import importlib.util
+    import sys
+
+    _spec = importlib.util.spec_from_file_location(__name__ + ".pivots", os.environ["JO_PIVOTS_SRC"])
+    pivots = importlib.util.module_from_spec(_spec)
+    sys.modules[__name__ + ".pivots"] = pivots
+    _spec.loader.exec_module(pivots)
+else:
+    from . import pivots
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 # JO_ORACLE_SRC / JO_ORACLE_BUILD: a hook for the mutation tests, which build a

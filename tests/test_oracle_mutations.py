@@ -18,6 +18,12 @@ Cases, by the passage each one breaks:
   App. A            DRDSSQ's large-entry scale and its even exponent;
   Eq. (2.1)         the QR preprocessing's reflector;
   the SVD adjoint   the sign of F, the V term, the projector term.
+The same is done for the oracle's pivot generator (pivots.py, JO_PIVOTS_SRC),
+against its pins and the bit-exact comparison with the library's tables:
+  Sec. 3            R_n enumerated as C_n, the order of Alg. 3.2's NE/SW and
+                    NW/SE pairs, the reverse without the in-step reversal, the
+                    modulus strategy's idle index, the dynamic ordering's tie
+                    break and its (lower, higher) pairs.
 Not a case: the sign of tan*h_pq in the P2 sort's new diagonal (reading R1).
 The annihilating rotation (|phi| <= pi/4) never reverses the order of h_pp and
 h_qq, and both new diagonal entries move by the same tan*h_pq, so comparing the
@@ -77,29 +83,58 @@ MUTATIONS = {
 }
 
 
-def _run_pins(text: str):
+PIVOTS_SRC = os.path.join(ROOT, "oracle", "pivots.py")
+PIVOT_PINS = ["tests/test_oracle_pivots.py", "tests/test_abi.py"]
+PIVOT_MUTATIONS = {
+    "R_n enumerated column-wise": ("return [(i, j) for i in range(n) for j in range(i + 1, n)]",
+                                   "return [(i, j) for j in range(n) for i in range(j)]"),
+    "Alg. 3.2 NE/SW order swapped": ('step += [ne, sw] if kind == "R" else [sw, ne]',
+                                     'step += [sw, ne] if kind == "R" else [ne, sw]'),
+    "Alg. 3.2 NW/SE order swapped": ("step += [(2 * p, 2 * q), (2 * p + 1, 2 * q + 1)]",
+                                     "step += [(2 * p + 1, 2 * q + 1), (2 * p, 2 * q)]"),
+    "reverse keeps the in-step order": ("return [list(reversed(step)) for step in reversed(strategy)]",
+                                        "return [list(step) for step in reversed(strategy)]"),
+    "modulus idle index": ("istar = next(i for i in range(N) if (2 * i) % N == s)",
+                           "istar = next(i for i in range(N) if (2 * i + 1) % N == s)"),
+    "norm order ties reversed": ("return sorted(idx, key=lambda B: (-float(block_norms[B]), B))",
+                                 "return sorted(idx, key=lambda B: (-float(block_norms[B]), -B))"),
+    "remap without (lower, higher)": ("[(min(perm[p], perm[q]), max(perm[p], perm[q])) for (p, q) in step]",
+                                      "[(perm[p], perm[q]) for (p, q) in step]"),
+}
+
+
+def _run_pins(file_name: str, env_vars, pins, text: str):
     d = tempfile.mkdtemp(prefix="jo_mutant_")
     try:
-        src = os.path.join(d, "jacobi_oracle.c")
+        src = os.path.join(d, file_name)
         with open(src, "w") as f:
             f.write(text)
-        env = dict(os.environ, JO_ORACLE_SRC=src, JO_ORACLE_BUILD=os.path.join(d, "_build"))
-        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+        env = dict(os.environ, **{k: v.format(src=src, dir=d) for k, v in env_vars.items()})
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
         return r.returncode, r.stdout[-2500:] + r.stderr[-1000:]
     finally:
         shutil.rmtree(d, ignore_errors=True)
 
 
-def test_pins_catch_every_planted_mistake():
-    base = open(SRC).read()
+def _check(path, mutations, file_name, env_vars, pins):
+    base = open(path).read()
     cases = {"unmodified copy": base}
-    for name, (old, new) in MUTATIONS.items():
+    for name, (old, new) in mutations.items():
         assert base.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
         cases[name] = base.replace(old, new)
+    run = lambda text: _run_pins(file_name, env_vars, pins, text)     # noqa: E731
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        results = dict(zip(cases, ex.map(_run_pins, cases.values())))
+        results = dict(zip(cases, ex.map(run, cases.values())))
     rc, out = results.pop("unmodified copy")
     assert rc == 0, out
     survivors = [name for name, (code, _) in results.items() if code == 0]
     assert not survivors, f"planted mistakes no pin catches: {survivors}"
+
+
+def test_pins_catch_every_planted_mistake():
+    _check(SRC, MUTATIONS, "jacobi_oracle.c", {"JO_ORACLE_SRC": "{src}", "JO_ORACLE_BUILD": "{dir}/_build"}, PINS)
+
+
+def test_pivot_pins_catch_every_planted_mistake():
+    _check(PIVOTS_SRC, PIVOT_MUTATIONS, "pivots.py", {"JO_PIVOTS_SRC": "{src}"}, PIVOT_PINS)
