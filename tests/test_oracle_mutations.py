@@ -11,12 +11,16 @@ Cases, by the passage each one breaks:
                     cs_2 form of the hyperbolic cosh, the small-angle shortcut;
   Eqs. (4.1)/(4.2)  its application: the FMA signs, the multiply by cs;
   Sec. 4.3          the relative test (|h_pq|), the P2 sort's direction in
-                    either J block, V's rotation and swap;
+                    either J block, V's rotation and swap, the hyperbolic
+                    type at the J boundary;
   Eq. (2.7), 4.1    the Gram entry's operands, the Cholesky update and pivot;
   Eq. (2.9)         the update's right factor transposed;
   Sec. 4 (Sigma)    the column norm's square root;
   App. A            DRDSSQ's large-entry scale and its even exponent;
-  Eq. (2.1)         the QR preprocessing's reflector;
+  Sec. 4.5          the stop rules of the pointwise and the block method;
+  readings R5, R7   a zero Cholesky pivot not counted, border columns rotated;
+  Eq. (2.1)         the QR preprocessing's pivot choice, reflector and tau, and
+                    the order in which Q is applied;
   the SVD adjoint   the sign of F, the V term, the projector term.
 The same is done for the oracle's pivot generator (pivots.py, JO_PIVOTS_SRC),
 against its pins and the bit-exact comparison with the library's tables:
@@ -80,6 +84,18 @@ MUTATIONS = {
     "adjoint V term dropped": ("v = F * a * s[j] + s[i] * (F * c);", "v = F * a * s[j];"),
     "adjoint projector term dropped": ("Z[r + (size_t)j * m] = (dU[r + (size_t)j * m] - a) / s[j];",
                                        "Z[r + (size_t)j * m] = dU[r + (size_t)j * m] / s[j];"),
+    "pointwise stop after any sweep (4.5)": ("if (rot == 0) { converged = 1; ++sweep; break; }",
+                                             "if (rot >= 0) { converged = 1; ++sweep; break; }"),
+    "block stop after any sweep (4.5)": ("if (B == 0) { converged = 1; ++sweep; break; }",
+                                         "if (B >= 0) { converged = 1; ++sweep; break; }"),
+    "border columns rotated (R7)": ("        return 0;                                       /* R7 */",
+                                    "        ;                                               /* R7 */"),
+    "hyperbolic type boundary (Sec. 4.3)": ("int t = (k < nplus && l >= nplus) ? -1 : 1;",
+                                            "int t = (k < nplus && l > nplus) ? -1 : 1;"),
+    "zero Cholesky pivot not a breakdown (R5)": ("if (!(d > 0.0)) {", "if (d < 0.0) {"),
+    "QR pivot: smallest column (2.1)": ("if (nrm[k] > nrm[best]) best = k;", "if (nrm[k] < nrm[best]) best = k;"),
+    "QR tau sign (2.1)": ("tau[j] = (beta - alpha) / beta;", "tau[j] = (alpha - beta) / beta;"),
+    "Q applied in the wrong order (2.1)": ("for (int j = n - 1; j >= 0; --j) {", "for (int j = 0; j < n; ++j) {"),
 }
 
 
