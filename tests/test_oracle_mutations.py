@@ -28,6 +28,11 @@ against its pins and the bit-exact comparison with the library's tables:
                     NW/SE pairs, the reverse without the in-step reversal, the
                     modulus strategy's idle index, the dynamic ordering's tie
                     break and its (lower, higher) pairs.
+And for the oracle's Python layer (oracle/__init__.py, run on a copy of the
+tree): the final sort's direction in either J block, u_i = g_i / sigma_i, the
+HSVD's V = J W J, the identity border's rows and the columns after it, the QR
+preprocessing's R^T and its permutation of V, and the dynamic ordering's
+per-sweep ranking.
 Not a case: the sign of tan*h_pq in the P2 sort's new diagonal (reading R1).
 The annihilating rotation (|phi| <= pi/4) never reverses the order of h_pp and
 h_qq, and both new diagonal entries move by the same tan*h_pq, so comparing the
@@ -154,3 +159,52 @@ def test_pins_catch_every_planted_mistake():
 
 def test_pivot_pins_catch_every_planted_mistake():
     _check(PIVOTS_SRC, PIVOT_MUTATIONS, "pivots.py", {"JO_PIVOTS_SRC": "{src}"}, PIVOT_PINS)
+
+
+PY_PINS = ["tests/test_oracle_rotation.py", "tests/test_oracle_svd.py", "tests/test_oracle_adjoint.py",
+           "tests/test_oracle_quad.py", "tests/test_oracle_pivots.py"]
+PY_MUTATIONS = {
+    "final sort ascending": ('order = np.argsort(-s, kind="stable")', 'order = np.argsort(s, kind="stable")'),
+    "J- block sorted ascending": ('nplus + np.argsort(-s[nplus:], kind="stable")',
+                                  'nplus + np.argsort(s[nplus:], kind="stable")'),
+    "U not normalised": ("U = np.where(s[order] > 0, G[:, order] / s[order], 0.0)",
+                         "U = np.where(s[order] > 0, G[:, order], 0.0)"),
+    "HSVD V = W, not J W J": ("W = j[:, None] * W * j[None, :]", "W = W"),
+    "border identity in the top rows": ("B[m:, nplus:nplus + k] = np.eye(k)", "B[:k, nplus:nplus + k] = np.eye(k)"),
+    "columns after the border not shifted": ("B[:m, nplus + k:] = A[:, nplus:]", "B[:m, nplus:n] = A[:, nplus:]"),
+    "QR: the method on R, not R^T": ("RT = np.asfortranarray(np.triu(W[:n, :]).T)",
+                                     "RT = np.asfortranarray(np.triu(W[:n, :]))"),
+    "QR: V without the column permutation": ("V[piv, :] = X", "V[:, :] = X"),
+    "dynamic ordering not re-ranked": ("perm = pivots.norm_order(block_norms(G, b))", "perm = list(range(nb))"),
+}
+
+
+def _run_tree(text: str):
+    """The pins on a copy of the tree whose oracle/__init__.py is `text`."""
+    d = tempfile.mkdtemp(prefix="jo_mutant_tree_")
+    try:
+        skip = shutil.ignore_patterns("_build", "_lib", "__pycache__", "csrc", "*.so")
+        for sub in ("oracle", "tests", "paper_1401_2720_gb300"):
+            shutil.copytree(os.path.join(ROOT, sub), os.path.join(d, sub), ignore=skip)
+        with open(os.path.join(d, "oracle", "__init__.py"), "w") as f:
+            f.write(text)
+        env = {k: v for k, v in os.environ.items() if not k.startswith("JO_")}
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PY_PINS],
+                           cwd=d, env=env, capture_output=True, text=True, timeout=900)
+        return r.returncode, r.stdout[-2500:] + r.stderr[-1000:]
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+
+
+def test_python_layer_pins_catch_every_planted_mistake():
+    base = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    cases = {"unmodified copy": base}
+    for name, (old, new) in PY_MUTATIONS.items():
+        assert base.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+        cases[name] = base.replace(old, new)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        results = dict(zip(cases, ex.map(_run_tree, cases.values())))
+    rc, out = results.pop("unmodified copy")
+    assert rc == 0, out
+    survivors = [name for name, (code, _) in results.items() if code == 0]
+    assert not survivors, f"planted mistakes no pin catches: {survivors}"

@@ -173,6 +173,36 @@ def test_block_method_with_identity_border(mn):
     s = np.sort(np.sqrt((r["G"][:, keep] ** 2).sum(0)))[::-1]
     sl = np.linalg.svd(A, compute_uv=False)
     assert np.max(np.abs(s - sl)) <= 50 * np.sqrt(max(n, 2)) * EPS * sl[0]
+    # the method's fixed point: the columns of the bordered G, border ones
+    # included, are mutually orthogonal, and the matrix columns keep exactly
+    # zero border rows
+    Gc = r["G"][:, np.linalg.norm(r["G"], axis=0) > 0]
+    H = Gc.T @ Gc
+    d = np.sqrt(np.diag(H))
+    assert np.abs(H / np.outer(d, d) - np.eye(H.shape[0])).max() <= 50 * np.sqrt(B.shape[0]) * EPS
+    assert not np.any(r["G"][m:, keep])
+
+
+@pytest.mark.parametrize("mnp", [(30, 13, 5), (41, 22, 0), (25, 10, 10), (36, 19, 18)])
+def test_hsvd_block_method_with_identity_border(mnp):
+    """HSVD of a bordered input (the border goes in at the J boundary): the
+    matrix columns' signed squared norms are the non-zero eigenvalues of
+    G J G^T (Eq. (2.10)), and the border columns leave as unit columns."""
+    m, n, npl = mnp
+    rng = np.random.default_rng(m + n + npl)
+    G = np.asfortranarray(rng.standard_normal((m, n)))
+    B, bd, npl_w = O.bordered(G, 4, npl)
+    r = O.block_svd(B, 4, strategy="modulus", nplus=npl_w, border=bd)
+    assert r["converged"]
+    keep = np.ones(B.shape[1], bool)
+    keep[bd[0]:bd[1]] = False
+    sign = np.where(np.arange(B.shape[1]) < npl_w, 1.0, -1.0)
+    mine = np.sort(((r["G"] ** 2).sum(0) * sign)[keep])
+    j = np.where(np.arange(n) < npl, 1.0, -1.0)
+    lam = np.linalg.eigvalsh(G @ np.diag(j) @ G.T)
+    lam = np.sort(lam[np.argsort(-np.abs(lam))][:n])
+    assert np.max(np.abs(mine - lam)) <= 1e-12 * np.abs(lam).max()
+    assert np.allclose(np.linalg.norm(r["G"][:, bd[0]:bd[1]], axis=0), 1.0, rtol=0, atol=4 * EPS)
     assert np.all(r["G"][m:, keep] == 0.0)
     assert np.array_equal(r["G"][:, ~keep], B[:, ~keep])     # the border never moves
 
