@@ -158,6 +158,9 @@ def test_pins_catch_every_planted_mistake():
 
 
 def test_pivot_pins_catch_every_planted_mistake():
+    from paper_1401_2720_gb300 import build_ext
+
+    build_ext.build()       # once here, so the parallel runs of tests/test_abi.py find it built
     _check(PIVOTS_SRC, PIVOT_MUTATIONS, "pivots.py", {"JO_PIVOTS_SRC": "{src}"}, PIVOT_PINS)
 
 
