@@ -43,3 +43,29 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_is_silent_on_other_ranks():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_clock_sampler_parses_nvidia_smi_lines():
+    """The clocks record of the benchmark line: median SM clock under load, the
+    maximum, and the throttle reasons seen in any sample."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def communicate(self, timeout=None):
+            lines = ["2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+                     "2055, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active",
+                     "2070, 2070, 1250.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                     "[N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                     "garbage"]
+            return "\n".join(lines), ""
+
+    cs = bench.ClockSampler(0)
+    cs.proc = FakeProc()
+    rec = cs.stop()
+    assert rec == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    cs2 = bench.ClockSampler(0)
+    assert cs2.stop() is None                                   # no sampler ran
