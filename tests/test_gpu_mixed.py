@@ -7,7 +7,6 @@ disagreement between two orderings, orthogonality <= 50 n 2^-53.
 """
 import numpy as np
 import pytest
-import torch
 
 import oracle as O
 from paper_1401_2720_gb300 import inputs as I
